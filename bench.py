@@ -1,0 +1,327 @@
+"""Benchmark: BP3 (scalar Poisson, Gauss-Legendre q = p+2) FP64 Jacobi-PCG on
+perturbed brick meshes of the unit cube, orders p = 1..8 (section
+"Benchmarks"; throughput metric of the libCEED BP3 figures: DOFs x CG
+iterations / s).
+
+One step = for every order p in the sweep, a fixed number of graph-captured
+Jacobi-PCG iterations (apply + vector updates + reductions, the whole hot
+path) on that order's mesh of about --dofs global nodes.  `value` is the
+aggregate GDOF/s = sum_p N_p * iterations / time, with every input resident
+in HBM; `e2e` repeats it through the public API with the right-hand sides
+copied from pinned host memory and the solutions copied back every step.
+
+`--impl reference` times the FP64 CPU oracle (test infrastructure) on a
+bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fem_inputs  # noqa: E402
+
+METRIC = "BP3 FP64 Jacobi-PCG throughput (DOFs x CG iterations / s), p=1..8 sweep"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dofs", type=float, default=5e7)
+    ap.add_argument("--orders", default="1-8")
+    ap.add_argument("--iters", type=int, default=10, help="CG iterations per order per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def orders(spec):
+    if "-" in spec:
+        a, b = spec.split("-")
+        return list(range(int(a), int(b) + 1))
+    return [int(s) for s in spec.split(",")]
+
+
+def workload(args):
+    ps = orders(args.orders)
+    return [(p, fem_inputs.bp3_mesh_n(args.dofs, p)) for p in ps]
+
+
+def algorithmic(p, n):
+    """Per apply of BP3 (q = p+2): FP64 bytes that must move and flops."""
+    P, q = p + 1, p + 2
+    E = n ** 3
+    N = (p * n + 1) ** 3
+    bytes_ = 8 * N + 8 * N + 4 * E * P ** 3 + 8 * E * q ** 3 * 6
+    flops = E * (2 * (2 * (q * P ** 3 + q * q * P * P + q ** 3 * P) + 6 * q ** 4) + 18 * q ** 3)
+    return N, E, bytes_, flops
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush(); self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 FMA peak derived from unit counts and clock: 148 SMs x 2 FP64 FMA
+    lanes... per SM per clock x 2 flops; see the design doc (the B300 nominal is
+    1.25 TFLOP/s)."""
+    return 148 * FP64_FMA_PER_SM_CLK * 2 * (sm_mhz or 2032.0) * 1e6 / 1e12
+
+
+FP64_FMA_PER_SM_CLK = 2.0
+
+
+def cpu_baseline(work, iters, seconds, seed=0):
+    """Oracle (brute-force FP64 apply, as it stands) on a bounded sample of
+    elements of every order's mesh; extrapolated to the step's DOF-iterations."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    total_dof_it, total_t, sample = 0.0, 0.0, []
+    per = seconds / len(work)
+    for p, n in work:
+        N, E, _, _ = algorithmic(p, n)
+        # a small mesh of the same order and element shape; time elements until `per` s
+        m = fem_inputs.box_mesh(min(n, 6), p, perturb=0.1, seed=seed)
+        op = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, p + 2, nthreads=cores)
+        x = fem_inputs.rhs_uniform(m["N"], None, seed=seed)
+        ne, t = 0, 0.0
+        chunk = m["E"]
+        while t < per:
+            t0 = time.perf_counter()
+            op.apply(x)
+            t += time.perf_counter() - t0
+            ne += chunk
+        t_elem = t / ne
+        total_t += t_elem * E * iters
+        total_dof_it += N * iters
+        sample.append("p=%d: %d elements in %.1fs" % (p, ne, t))
+    return {"value": total_dof_it / total_t / 1e9, "unit": "GDOF/s", "cores": cores,
+            "kind": "oracle", "sample": "; ".join(sample) +
+            " (brute-force element apply, extrapolated to every element x iterations)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    work = workload(args)
+    base = cpu_baseline(work, args.iters, max(2.0, args.cpu_seconds / 3))
+    ms = 0.0
+    steps = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        b = cpu_baseline(work, args.iters, max(1.0, args.cpu_seconds / 5), seed=s)
+        if s >= args.warmup:
+            steps.append(b["value"])
+        ms += 0.0 * (time.perf_counter() - t0)
+    val = float(np.median(steps))
+    N_tot = sum(algorithmic(p, n)[0] for p, n in work)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GDOF/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": N_tot * args.iters / (val * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, work),
+            "cpu_baseline": dict(base, value=val),
+            "e2e": {"value": val, "unit": "GDOF/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def config(args, work):
+    return {"workload": "BP3 FP64 Jacobi-PCG, Gauss-Legendre q=p+2, perturbed unit-cube "
+                        "brick meshes of about %.0e DOFs per order" % args.dofs,
+            "orders": [p for p, _ in work], "elements_per_dim": [n for _, n in work],
+            "dofs": [algorithmic(p, n)[0] for p, n in work],
+            "cg_iterations_per_order": args.iters, "parallelism": "replicas",
+            "l2": "inputs larger than L2 (no flush needed)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2109_04996_b300 import build as fembuild
+    fembuild.build()
+    import paper_2109_04996_b300 as fem
+
+    work = workload(args)
+    stream = torch.cuda.current_stream()
+    ops = []
+    for p, n in work:
+        m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=100 + p)
+        gm = fem.Mesh(m, stream=stream)
+        op = fem.Operator.bake_off(gm, "BP3")
+        b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=200 + p)).cuda()
+        x = torch.zeros_like(b)
+        ops.append((p, n, gm, op, b, x))
+        del m
+    torch.cuda.synchronize()
+
+    def step():
+        for p, n, gm, op, b, x in ops:
+            x.zero_()
+            st = op.cg(b, x, precond=fem.PC_JACOBI, maxit=args.iters, rtol=0.0, use_graph=True)
+            assert st["iterations"] == args.iters, st
+
+    for _ in range(args.warmup):
+        step()
+    clk = Clocks()
+    clk.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        dist.barrier()
+    clocks = clk.stop()
+    dof_it = sum(algorithmic(p, n)[0] for p, n in work) * args.iters
+    value = dof_it * world / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host RHS in, solution out, every step
+    hb = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True).copy_(b.cpu())
+          for (_, _, _, _, b, _) in ops]
+    hx = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True)
+          for (_, _, _, _, b, _) in ops]
+
+    def step_e2e():
+        for k, (p, n, gm, op, b, x) in enumerate(ops):
+            b.copy_(hb[k], non_blocking=True)
+            x.zero_()
+            op.cg(b, x, precond=fem.PC_JACOBI, maxit=args.iters, rtol=0.0, use_graph=True)
+            hx[k].copy_(x, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    step_e2e()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    h2d = sum(8 * b.numel() for (_, _, _, _, b, _) in ops)
+
+    # dominant kernel: the fused apply, timed per launch with events on its stream
+    per_p = []
+    tot_time, tot_flop, tot_bytes = 0.0, 0.0, 0.0
+    for p, n, gm, op, b, x in ops:
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.apply(b, y)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a0.record(stream)
+        for _ in range(reps):
+            op.apply(b, y)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_apply = a0.elapsed_time(a1) / reps * 1e-3
+        N, E, by, fl = algorithmic(p, n)
+        per_p.append({"p": p, "N": N, "apply_ms": t_apply * 1e3,
+                      "apply_gdofs": N / t_apply / 1e9,
+                      "apply_tflops": fl / t_apply / 1e12,
+                      "apply_hbm_gbs": by / t_apply / 1e9})
+        tot_time += t_apply; tot_flop += fl; tot_bytes += by
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    fp64_peak = fp64_peak_tflops(clocks.get("sm_mhz"))
+    achieved = tot_flop / tot_time / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "kernel": "fem_apply_kernel (FP64, all orders of the sweep)",
+                "hbm_achieved_gbs": tot_bytes / tot_time / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": tot_bytes / tot_time / 1e9 / hbm_peak,
+                "peak_source": "FP64 peak derived from unit counts x median SM clock (DESIGN.md);"
+                               " HBM from MEASURED_PEAKS.json"}
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, work),
+            "e2e": {"value": dof_it * world / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+            "gpu_launches": len(ops) * (3 + 3 * args.iters) * args.steps,
+            "roofline": roofline, "clocks": clocks, "per_order": per_p}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(work, args.iters, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * fem.h -- C ABI of a B300-native (sm_103a) library for matrix-free,
+ * partially assembled high-order finite element operators on hexahedral
+ * meshes:  y = G^T B^T D B G x  (Kolev et al., "Efficient Exascale
+ * Discretizations: High-Order Finite Element Methods", section "libCEED",
+ * finite element operator decomposition), applied inside conjugate gradients
+ * for the bake-off problems BP1-BP6 (section "Benchmarks").
+ *
+ *   G  element restriction: gather of global (L-vector) values into element
+ *      (E-vector) values, and its transpose, a scatter-add;
+ *   B  tensor-product basis: interpolation / gradients from the (p+1)^3
+ *      Gauss-Lobatto nodes of an element to its q^3 quadrature points,
+ *      evaluated by sum factorization (section "Benchmarks");
+ *   D  pointwise data at quadrature points: w det J (mass, BP1/BP2) or the
+ *      symmetric w det J J^{-1} J^{-T} (diffusion, BP3-BP6), times an optional
+ *      coefficient kappa(x).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns fem_status; FEM_OK == 0.  On failure the
+ *    message of the calling thread's last error is fem_last_error().  No call
+ *    aborts, exits or throws across the ABI.
+ *  - Arguments named *_host are host pointers and are copied before the call
+ *    returns.  All other array arguments are DEVICE pointers owned by the
+ *    caller; the library never frees them and keeps no reference after the
+ *    call returns (unless stated).
+ *  - Work is ordered on the CUDA stream given to fem_op_create (NULL = the
+ *    legacy default stream).  Calls return without synchronizing the host
+ *    unless stated (fem_cg_solve and fem_solve_refined copy their statistics
+ *    back and therefore synchronize).
+ *  - Vectors are contiguous float64 (float32 where stated) of length
+ *    ncomp * N, component-major: entry c*N + i is component c of node i.
+ *  - Local node (a, b, c) of an element (a fastest) is entry a + P b + P^2 c of
+ *    its row of elem_nodes, P = p + 1; vertex v = vi + 2 vj + 4 vk of a brick
+ *    likewise (lexicographic tensor order).
+ *  - Supported orders: 1 <= p <= 8.  Quadrature: FEM_GAUSS with q = p + 2
+ *    (BP1-BP4) or q = p + 1, FEM_LOBATTO with q = p + 1 (BP5/BP6,
+ *    collocated).
+ *  - Handles are not thread safe: one host thread at a time per handle.
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fem_status;
+enum {
+  FEM_OK = 0,
+  FEM_EINVAL = 1,      /* bad argument: order, quadrature, sizes, null pointer */
+  FEM_ENOMEM = 2,      /* device or host allocation failed */
+  FEM_ECUDA = 3,       /* a CUDA runtime call failed */
+  FEM_EBREAKDOWN = 4,  /* CG breakdown: p^T A p <= 0 or a non-finite scalar */
+  FEM_ENOCONV = 5,     /* iteration limit reached before the tolerance */
+  FEM_ETIMEOUT = 6,    /* a bounded device-side wait expired */
+  FEM_EDEVICE = 7      /* a kernel raised its device error word (bad index) */
+};
+
+enum { FEM_MASS = 0, FEM_DIFFUSION = 1 };      /* D: B_ij or A_ij (section "Benchmarks") */
+enum { FEM_GAUSS = 0, FEM_LOBATTO = 1 };       /* quadrature family */
+enum { FEM_F64 = 0, FEM_F32 = 1 };             /* arithmetic of the apply */
+enum { FEM_PC_NONE = 0, FEM_PC_JACOBI = 1, FEM_PC_LEARNED = 2 };
+
+typedef struct fem_mesh fem_mesh;
+typedef struct fem_op fem_op;
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char *fem_last_error(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int fem_version(void);
+
+/* ---------------------------------------------------------------- tables */
+
+/* 1D tables of the tensor basis (section "Benchmarks": Gauss-Legendre q = p+2
+ * for BP1-BP4, Gauss-Lobatto-Legendre q = p+1 for BP5/BP6), host output:
+ *   nodes_host[P]     Gauss-Lobatto nodes of the Lagrange basis on [-1, 1]
+ *   qpts_host[q], qwts_host[q]   quadrature points and weights
+ *   interp_host[q*P]  l_a(r_k) at row k, column a
+ *   grad_host[q*P]    l_a'(r_k)
+ * Any output pointer may be NULL.  FEM_EINVAL for p or q out of range. */
+fem_status fem_basis_tables(int p, int q, int quad, double *nodes_host,
+                            double *qpts_host, double *qwts_host,
+                            double *interp_host, double *grad_host);
+
+/* ---------------------------------------------------------------- mesh */
+
+/* Coordinates of the Q_p nodes of trilinear bricks (host, setup only): node
+ * (a,b,c) of element e is the trilinear map of the element's 8 vertices at
+ * the tensor Gauss-Lobatto point (z_a, z_b, z_c) (the isoparametric bricks of
+ * section "Benchmarks").  vert_xyz_host [nvert][3], elem_verts_host [E][8],
+ * elem_nodes_host [E][P^3]; writes node_xyz_host [N][3]. */
+fem_status fem_mesh_nodes_from_vertices(int p, int64_t E, int64_t nvert,
+                                        const double *vert_xyz_host,
+                                        const int32_t *elem_verts_host,
+                                        const int32_t *elem_nodes_host,
+                                        int64_t N, double *node_xyz_host);
+
+/* Upload a Q_p mesh: connectivity elem_nodes_host [E][P^3] (global node ids in
+ * [0, N)), node coordinates node_xyz_host [N][3] and the Dirichlet marker
+ * dirichlet_host [N] (1 = constrained node; NULL = none).  The element
+ * restriction G is this connectivity (section "libCEED").  Indices are
+ * checked on the host (FEM_EINVAL if out of range).  stream: cudaStream_t or
+ * NULL. */
+fem_status fem_mesh_create(int p, int64_t N, int64_t E,
+                           const int32_t *elem_nodes_host,
+                           const double *node_xyz_host,
+                           const uint8_t *dirichlet_host, void *stream,
+                           fem_mesh **out);
+fem_status fem_mesh_destroy(fem_mesh *mesh);
+
+/* ---------------------------------------------------------------- operator */
+
+/* Create an operator on a mesh and compute its pointwise data D (qdata) and
+ * the diagonal of the assembled matrix on the GPU in FP64:
+ *   kind   FEM_MASS (B_ij = int phi_i phi_j) or FEM_DIFFUSION
+ *          (A_ij = int grad phi_i . grad phi_j), section "Benchmarks";
+ *   quad, q  see "Supported orders" above;
+ *   ncomp  1 (BP1/BP3/BP5) or 3 (BP2/BP4/BP6), the same scalar operator on
+ *          each component;
+ *   prec   FEM_F64: the apply computes in FP64 with FP64 qdata;
+ *          FEM_F32: an additional FP32 copy of the qdata is kept and
+ *          fem_op_apply_f32 becomes available (fem_op_apply stays FP64);
+ *   rff_host  NULL (kappa = 1) or the [M][4] rows (w_x, w_y, w_z, b) of
+ *          kappa(x) = exp(sigma sqrt(2/M) sum_m cos(w_m . x + b_m)), a random
+ *          Fourier feature draw of a Gaussian random field; the data D is
+ *          multiplied by kappa at each physical quadrature point.
+ * The mesh must outlive the operator.  Work goes to the mesh's stream. */
+fem_status fem_op_create(const fem_mesh *mesh, int kind, int quad, int q,
+                         int ncomp, int prec, const double *rff_host, int M,
+                         double sigma, fem_op **out);
+fem_status fem_op_destroy(fem_op *op);
+
+/* Sizes: N nodes, E elements, ncomp, P = p+1, q, and the device bytes held. */
+fem_status fem_op_sizes(const fem_op *op, int64_t *N, int64_t *E, int *ncomp,
+                        int *P, int *q, int64_t *device_bytes);
+
+/* y = G^T B^T D B G x, the unconstrained operator (no Dirichlet rows),
+ * FP64, one fused kernel: gather, sum-factorized interpolation / gradients,
+ * pointwise D, transposes and an atomic scatter-add (section "libCEED",
+ * fused single-kernel operator).  x, y: device [ncomp*N]; y is overwritten;
+ * x and y must not alias. */
+fem_status fem_op_apply(fem_op *op, const double *x, double *y);
+
+/* Same in FP32 arithmetic with FP32 qdata (operator created with FEM_F32). */
+fem_status fem_op_apply_f32(fem_op *op, const float *x, float *y);
+
+/* y = sum over the listed elements of G_e^T B^T D B G_e x (FP64): the operator
+ * restricted to a subset of elements.  elems: device int32 [n]; y overwritten. */
+fem_status fem_op_apply_elements(fem_op *op, const int32_t *elems, int64_t n,
+                                 const double *x, double *y);
+
+/* diag(A): device [ncomp*N] FP64 diagonal of the assembled operator
+ * (computed at create by sum factorization of squared 1D tables). */
+fem_status fem_op_diagonal(fem_op *op, double *d);
+
+/* Copy the FP64 qdata of element e to host: mass [q^3] = w det J kappa;
+ * diffusion [6][q^3] = (11, 22, 33, 23, 13, 12) entries of
+ * w det J kappa J^{-1} J^{-T}; quadrature point (i,j,k) at i + q j + q^2 k. */
+fem_status fem_op_qdata_host(fem_op *op, int64_t e, double *out_host);
+
+/* Manufactured load b_i = int phi_i f dV on the GPU (same quadrature as the
+ * operator): which = 0: f = sin(pi x) sin(pi y) sin(pi z) (BP1/BP2);
+ * which = 1: f = 3 pi^2 sin sin sin (Poisson load of u = sin sin sin).
+ * b: device [N] (scalar). */
+fem_status fem_op_rhs(fem_op *op, int which, double *b);
+
+/* ---------------------------------------------------------------- solvers */
+
+typedef struct {
+  int precond;        /* FEM_PC_NONE, FEM_PC_JACOBI or FEM_PC_LEARNED */
+  int maxit;          /* iteration cap (inner iterations for refinement) */
+  double rtol;        /* stop when ||r||_2 <= rtol ||b||_2; 0 = run maxit */
+  int use_graph;      /* 1: device-side loop in one CUDA graph (conditional
+                         WHILE node); 0: one host launch sequence per step */
+  double inner_rtol;  /* fem_solve_refined: relative tolerance of each inner
+                         FP32 solve */
+  int max_outer;      /* fem_solve_refined: outer FP64 refinement steps cap */
+} fem_cg_opts;
+
+typedef struct {
+  int iterations;     /* CG iterations (total inner iterations if refined) */
+  int outer;          /* refinement steps taken (0 for fem_cg_solve) */
+  int status;         /* FEM_OK, FEM_ENOCONV or FEM_EBREAKDOWN */
+  double rnorm;       /* final ||r||_2 of the recursive residual */
+  double bnorm;       /* ||b||_2 over the unconstrained nodes */
+  double true_rel;    /* refined: ||b - A_64 x|| / ||b|| in FP64 at exit */
+} fem_cg_stats;
+
+/* Preconditioned CG (section "Benchmarks": CG on the BP systems; diagonal
+ * preconditioner as in Nekbone, section "Miniapps") on the Dirichlet-
+ * constrained system  (M A M + (I - M)) x = b,  M = interior mask, FP64 apply.
+ * b, x: device [ncomp*N]; x is the initial guess on entry (its Dirichlet
+ * entries are set to 0) and the solution on exit.  Scalars stay on the
+ * device; with use_graph = 1 the whole loop is one graph launch.  Copies the
+ * statistics back (synchronizes).  Returns FEM_OK, FEM_ENOCONV (maxit reached
+ * with rtol > 0) or FEM_EBREAKDOWN. */
+fem_status fem_cg_solve(fem_op *op, const double *b, double *x,
+                        const fem_cg_opts *opts, fem_cg_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM_H */

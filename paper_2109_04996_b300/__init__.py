@@ -1,0 +1,240 @@
+"""B300-native matrix-free high-order finite element operators (CEED bake-off
+problems BP1-BP6, Kolev et al., sections "Benchmarks" and "libCEED").
+
+A thin ctypes binding over libfem.so (C ABI declared in include/fem.h):
+argument marshalling only; every step of the operator and the solvers runs in
+the library's CUDA kernels.  PyTorch provides device memory and the stream.
+The library must be built (``python -m paper_2109_04996_b300.build``); there
+is no fallback when it is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libfem.so")
+
+MASS, DIFFUSION = 0, 1
+GAUSS, LOBATTO = 0, 1
+F64, F32 = 0, 1
+PC_NONE, PC_JACOBI, PC_LEARNED = 0, 1, 2
+STATUS = {0: "FEM_OK", 1: "FEM_EINVAL", 2: "FEM_ENOMEM", 3: "FEM_ECUDA", 4: "FEM_EBREAKDOWN",
+          5: "FEM_ENOCONV", 6: "FEM_ETIMEOUT", 7: "FEM_EDEVICE"}
+
+# The bake-off problems (section "Benchmarks"): kind, components, quadrature, q - p.
+BAKE_OFF = {
+    "BP1": (MASS, 1, GAUSS, 2), "BP2": (MASS, 3, GAUSS, 2),
+    "BP3": (DIFFUSION, 1, GAUSS, 2), "BP4": (DIFFUSION, 3, GAUSS, 2),
+    "BP5": (DIFFUSION, 1, LOBATTO, 1), "BP6": (DIFFUSION, 3, LOBATTO, 1),
+}
+
+
+class FemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class _CgOpts(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("use_graph", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("max_outer", ctypes.c_int)]
+
+
+class _CgStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("status", ctypes.c_int),
+                ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("true_rel", ctypes.c_double)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+def lib():
+    """Load libfem.so.  Raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise ImportError("libfem.so not built: run `python -m paper_2109_04996_b300.build`")
+    L = ctypes.CDLL(LIBPATH)
+    L.fem_last_error.restype = ctypes.c_char_p
+    sigs = {
+        "fem_basis_tables": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP],
+        "fem_mesh_nodes_from_vertices": [ctypes.c_int, _I64, _I64, _VP, _VP, _VP, _I64, _VP],
+        "fem_mesh_create": [ctypes.c_int, _I64, _I64, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+        "fem_mesh_destroy": [_VP],
+        "fem_op_create": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_int, _VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_VP)],
+        "fem_op_destroy": [_VP],
+        "fem_op_sizes": [_VP, _VP, _VP, _VP, _VP, _VP, _VP],
+        "fem_op_apply": [_VP, _VP, _VP],
+        "fem_op_apply_f32": [_VP, _VP, _VP],
+        "fem_op_apply_elements": [_VP, _VP, _I64, _VP, _VP],
+        "fem_op_diagonal": [_VP, _VP],
+        "fem_op_qdata_host": [_VP, _I64, _VP],
+        "fem_op_rhs": [_VP, ctypes.c_int, _VP],
+        "fem_cg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise FemError(rc, lib().fem_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a CUDA tensor (or host pointer of a numpy array)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def basis_tables(p, q, quad):
+    P = p + 1
+    out = [np.zeros(P), np.zeros(q), np.zeros(q), np.zeros((q, P)), np.zeros((q, P))]
+    _check(lib().fem_basis_tables(p, q, quad, *[_ptr(a) for a in out]))
+    return dict(nodes=out[0], qpts=out[1], qwts=out[2], interp=out[3], grad=out[4])
+
+
+def nodes_from_vertices(mesh):
+    """Q_p node coordinates [N, 3] of the trilinear bricks of a mesh dict."""
+    xyz = np.zeros((mesh["N"], 3))
+    vx = np.ascontiguousarray(mesh["vert_xyz"], dtype=np.float64)
+    ev = np.ascontiguousarray(mesh["elem_verts"], dtype=np.int32)
+    en = np.ascontiguousarray(mesh["elem_nodes"], dtype=np.int32)
+    _check(lib().fem_mesh_nodes_from_vertices(mesh["p"], mesh["E"], vx.shape[0], _ptr(vx),
+                                               _ptr(ev), _ptr(en), mesh["N"], _ptr(xyz)))
+    return xyz
+
+
+class Mesh:
+    """A Q_p hexahedral mesh resident on the GPU (elem_nodes, coordinates,
+    Dirichlet marker).  `mesh` is a dict as produced by fem_inputs.box_mesh;
+    node coordinates come from the library's own trilinear map unless given."""
+
+    def __init__(self, mesh, node_xyz=None, stream=None):
+        self.p = int(mesh["p"]); self.N = int(mesh["N"]); self.E = int(mesh["E"])
+        if node_xyz is None:
+            node_xyz = nodes_from_vertices(mesh)
+        self.node_xyz = np.ascontiguousarray(node_xyz, dtype=np.float64)
+        en = np.ascontiguousarray(mesh["elem_nodes"], dtype=np.int32)
+        dr = mesh.get("dirichlet")
+        dr = None if dr is None else np.ascontiguousarray(dr, dtype=np.uint8)
+        self.dirichlet = dr
+        h = _VP()
+        _check(lib().fem_mesh_create(self.p, self.N, self.E, _ptr(en), _ptr(self.node_xyz),
+                                     _ptr(dr), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fem_mesh_destroy(self._h)
+            self._h = None
+
+
+class Operator:
+    """y = G^T B^T D B G x on a Mesh (see include/fem.h, fem_op_create)."""
+
+    def __init__(self, mesh, kind, quad, q, ncomp=1, prec=F64, rff=None, sigma=1.0):
+        self.mesh = mesh
+        self.kind, self.quad, self.q, self.ncomp, self.prec = kind, quad, q, ncomp, prec
+        self.N, self.E, self.p = mesh.N, mesh.E, mesh.p
+        rff_a = None if rff is None else np.ascontiguousarray(rff, dtype=np.float64)
+        M = 0 if rff_a is None else rff_a.shape[0]
+        h = _VP()
+        _check(lib().fem_op_create(mesh._h, kind, quad, q, ncomp, prec, _ptr(rff_a), M,
+                                   float(sigma), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def bake_off(cls, mesh, name, prec=F64, **kw):
+        kind, ncomp, quad, dq = BAKE_OFF[name]
+        return cls(mesh, kind, quad, mesh.p + dq, ncomp=ncomp, prec=prec, **kw)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fem_op_destroy(self._h)
+            self._h = None
+
+    @property
+    def n(self):
+        return self.ncomp * self.N
+
+    def device_bytes(self):
+        b = ctypes.c_int64()
+        _check(lib().fem_op_sizes(self._h, None, None, None, None, None, ctypes.byref(b)))
+        return b.value
+
+    def apply(self, x, y=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().fem_op_apply(self._h, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_f32(self, x, y=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().fem_op_apply_f32(self._h, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_elements(self, elems, x, y=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().fem_op_apply_elements(self._h, _ptr(elems), elems.numel(), _ptr(x), _ptr(y)))
+        return y
+
+    def diagonal(self, d=None):
+        import torch
+        if d is None:
+            d = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(lib().fem_op_diagonal(self._h, _ptr(d)))
+        return d
+
+    def qdata(self, e):
+        nd = 6 if self.kind == DIFFUSION else 1
+        out = np.zeros((nd, self.q ** 3))
+        _check(lib().fem_op_qdata_host(self._h, e, _ptr(out)))
+        return out
+
+    def rhs(self, which, b=None):
+        import torch
+        if b is None:
+            b = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        _check(lib().fem_op_rhs(self._h, which, _ptr(b)))
+        return b
+
+    def cg(self, b, x, precond=PC_JACOBI, maxit=10000, rtol=1e-10, use_graph=True):
+        """Solve the Dirichlet-constrained system in place (x: initial guess
+        in, solution out).  Returns the statistics as a dict; raises FemError
+        on breakdown, returns status FEM_ENOCONV without raising."""
+        o = _CgOpts(precond, int(maxit), float(rtol), 1 if use_graph else 0, 0.0, 0)
+        st = _CgStats()
+        rc = lib().fem_cg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        if rc not in (0, 5):
+            _check(rc)
+        return dict(iterations=st.iterations, outer=st.outer, status=STATUS[st.status],
+                    rnorm=st.rnorm, bnorm=st.bnorm, true_rel=st.true_rel)

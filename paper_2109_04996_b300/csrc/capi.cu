@@ -1,0 +1,240 @@
+// C ABI entry points: mesh and operator lifecycle, apply, diagonal, solve.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "fem_internal.h"
+
+namespace {
+
+template <typename T>
+int dev_alloc(T **p, size_t count, int64_t *bytes) {
+  if (count == 0) count = 1;
+  if (cudaMalloc((void **)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    fem_set_error("device allocation of %zu bytes failed", sizeof(T) * count);
+    return FEM_ENOMEM;
+  }
+  *bytes += (int64_t)(sizeof(T) * count);
+  return FEM_OK;
+}
+
+__global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+}  // namespace
+
+extern "C" fem_status fem_mesh_create(int p, int64_t N, int64_t E, const int32_t *en,
+                                      const double *xyz, const uint8_t *dir, void *stream,
+                                      fem_mesh **out) {
+  if (!out) { fem_set_error("fem_mesh_create: out is NULL"); return FEM_EINVAL; }
+  *out = nullptr;
+  if (p < 1 || p + 1 > FEM_MAX_P) { fem_set_error("fem_mesh_create: p=%d not in [1, 8]", p); return FEM_EINVAL; }
+  if (N < 1 || E < 0 || (E > 0 && !en) || !xyz) { fem_set_error("fem_mesh_create: invalid sizes or NULL arrays"); return FEM_EINVAL; }
+  if (N > INT32_MAX) { fem_set_error("fem_mesh_create: N exceeds int32 node ids"); return FEM_EINVAL; }
+  const int P = p + 1, P3 = P * P * P;
+  for (int64_t i = 0; i < E * P3; i++)
+    if (en[i] < 0 || en[i] >= N) {
+      fem_set_error("fem_mesh_create: elem_nodes[%lld] = %d out of [0, %lld)", (long long)i, en[i], (long long)N);
+      return FEM_EINVAL;
+    }
+  fem_mesh *m = new fem_mesh();
+  m->p = p; m->P = P; m->N = N; m->E = E;
+  m->stream = (cudaStream_t)stream;
+  int rc;
+  if ((rc = dev_alloc(&m->d_elem_nodes, (size_t)E * P3, &m->bytes)) ||
+      (rc = dev_alloc(&m->d_xyz, (size_t)3 * N, &m->bytes)) ||
+      (rc = dev_alloc(&m->d_dirichlet, (size_t)N, &m->bytes))) {
+    fem_mesh_destroy(m);
+    return rc;
+  }
+  std::vector<double> soa((size_t)3 * N);
+  for (int64_t i = 0; i < N; i++)
+    for (int d = 0; d < 3; d++) soa[(size_t)d * N + i] = xyz[3 * i + d];
+  cudaError_t e = cudaMemcpyAsync(m->d_elem_nodes, en, sizeof(int32_t) * E * P3, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_xyz, soa.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) {
+    if (dir) e = cudaMemcpyAsync(m->d_dirichlet, dir, N, cudaMemcpyHostToDevice, m->stream);
+    else e = cudaMemsetAsync(m->d_dirichlet, 0, N, m->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    fem_set_error("fem_mesh_create: upload failed: %s", cudaGetErrorString(e));
+    fem_mesh_destroy(m);
+    return FEM_ECUDA;
+  }
+  *out = m;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_mesh_destroy(fem_mesh *m) {
+  if (!m) return FEM_OK;
+  cudaFree(m->d_elem_nodes); cudaFree(m->d_xyz); cudaFree(m->d_dirichlet);
+  delete m;
+  return FEM_OK;
+}
+
+
+extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q, int ncomp,
+                                    int prec, const double *rff, int M, double sigma,
+                                    fem_op **out) {
+  if (!out || !m) { fem_set_error("fem_op_create: NULL argument"); return FEM_EINVAL; }
+  *out = nullptr;
+  if (kind != FEM_MASS && kind != FEM_DIFFUSION) { fem_set_error("fem_op_create: bad kind %d", kind); return FEM_EINVAL; }
+  if (ncomp != 1 && ncomp != 3) { fem_set_error("fem_op_create: ncomp must be 1 or 3"); return FEM_EINVAL; }
+  if (prec != FEM_F64 && prec != FEM_F32) { fem_set_error("fem_op_create: bad precision %d", prec); return FEM_EINVAL; }
+  if (M < 0 || (M > 0 && !rff)) { fem_set_error("fem_op_create: bad coefficient arguments"); return FEM_EINVAL; }
+  fem_op *op = new fem_op();
+  if (fem_build_tables(m->p, q, quad, &op->tab) != FEM_OK) {
+    fem_set_error("fem_op_create: unsupported quadrature (p=%d, q=%d, quad=%d)", m->p, q, quad);
+    delete op;
+    return FEM_EINVAL;
+  }
+  op->mesh = m; op->kind = kind; op->quad = quad; op->q = q; op->ncomp = ncomp; op->prec = prec;
+  op->P = m->P; op->Q = q; op->N = m->N; op->E = m->E;
+  op->colloc = (quad == FEM_LOBATTO && q == m->P);
+  op->M = M; op->sigma = sigma;
+  const int P = op->P, Q = op->Q;
+  const int64_t Q3 = (int64_t)Q * Q * Q;
+  const int nd = kind == FEM_DIFFUSION ? 6 : 1;
+  int rc;
+  double *tab = nullptr;
+  float *tab32 = nullptr;
+  if ((rc = dev_alloc(&tab, TAB_SIZE, &op->bytes)) || (rc = dev_alloc(&tab32, TAB_SIZE, &op->bytes)) ||
+      (rc = dev_alloc(&op->d_qdata, (size_t)op->E * nd * Q3, &op->bytes)) ||
+      (rc = dev_alloc(&op->d_diag, (size_t)op->N, &op->bytes)) ||
+      (rc = dev_alloc(&op->d_partials, (size_t)4 * FEM_MAX_BLOCKS, &op->bytes)) ||
+      (rc = dev_alloc(&op->d_counter, 4, &op->bytes))) {
+    op->d_B = tab; op->d_B32 = tab32;
+    fem_op_destroy(op);
+    return rc;
+  }
+  op->d_B = tab + TAB_B; op->d_Dq = tab + TAB_DQ;
+  op->d_B32 = tab32 + TAB_B; op->d_Dq32 = tab32 + TAB_DQ;
+  std::vector<double> h(TAB_SIZE, 0.0);
+  std::vector<float> h32(TAB_SIZE, 0.0f);
+  memcpy(&h[TAB_B], op->tab.B, sizeof(double) * Q * P);
+  memcpy(&h[TAB_DQ], op->tab.Dq, sizeof(double) * Q * Q);
+  memcpy(&h[TAB_G], op->tab.G, sizeof(double) * Q * P);
+  memcpy(&h[TAB_W], op->tab.w, sizeof(double) * Q);
+  for (int i = 0; i < TAB_SIZE; i++) h32[i] = (float)h[i];
+  cudaStream_t s = m->stream;
+  cudaError_t e = cudaMemcpyAsync(tab, h.data(), sizeof(double) * TAB_SIZE, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tab32, h32.data(), sizeof(float) * TAB_SIZE, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(op->d_counter, 0, sizeof(unsigned) * 4, s);
+  if (e == cudaSuccess && M > 0) {
+    if ((rc = dev_alloc(&op->d_rff, (size_t)4 * M, &op->bytes))) { fem_op_destroy(op); return rc; }
+    e = cudaMemcpyAsync(op->d_rff, rff, sizeof(double) * 4 * M, cudaMemcpyHostToDevice, s);
+  }
+  if (e != cudaSuccess) {
+    fem_set_error("fem_op_create: upload failed: %s", cudaGetErrorString(e));
+    fem_op_destroy(op);
+    return FEM_ECUDA;
+  }
+  if ((rc = fem_setup_qdata(op)) || (rc = fem_setup_diagonal(op))) {
+    fem_op_destroy(op);
+    return rc;
+  }
+  if (prec == FEM_F32) {
+    const size_t nq = (size_t)op->E * nd * Q3;
+    if ((rc = dev_alloc(&op->d_qdata32, nq, &op->bytes))) { fem_op_destroy(op); return rc; }
+    if (nq > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qdata, op->d_qdata32, (int64_t)nq);
+  }
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fem_set_error("fem_op_create: setup kernels failed: %s", cudaGetErrorString(e));
+    fem_op_destroy(op);
+    return FEM_ECUDA;
+  }
+  *out = op;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_op_destroy(fem_op *op) {
+  if (!op) return FEM_OK;
+  fem_cg_free(op);
+  extern void fem_refine_free(fem_op *);
+  fem_refine_free(op);
+  if (op->d_B) cudaFree(op->d_B - TAB_B);
+  if (op->d_B32) cudaFree(op->d_B32 - TAB_B);
+  cudaFree(op->d_qdata); cudaFree(op->d_qdata32); cudaFree(op->d_diag); cudaFree(op->d_rff);
+  cudaFree(op->d_partials); cudaFree(op->d_counter);
+  delete op;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_op_sizes(const fem_op *op, int64_t *N, int64_t *E, int *ncomp, int *P,
+                                   int *q, int64_t *bytes) {
+  if (!op) { fem_set_error("fem_op_sizes: NULL operator"); return FEM_EINVAL; }
+  if (N) *N = op->N;
+  if (E) *E = op->E;
+  if (ncomp) *ncomp = op->ncomp;
+  if (P) *P = op->P;
+  if (q) *q = op->Q;
+  if (bytes) *bytes = op->bytes + op->mesh->bytes;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_op_apply(fem_op *op, const double *x, double *y) {
+  if (!op || !x || !y || x == y) { fem_set_error("fem_op_apply: invalid arguments"); return FEM_EINVAL; }
+  FEM_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * op->N * op->ncomp, op->stream()));
+  return fem_launch_apply_f64(op, x, y, nullptr, op->E, nullptr);
+}
+
+extern "C" fem_status fem_op_apply_f32(fem_op *op, const float *x, float *y) {
+  if (!op || !x || !y || x == y) { fem_set_error("fem_op_apply_f32: invalid arguments"); return FEM_EINVAL; }
+  FEM_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(float) * op->N * op->ncomp, op->stream()));
+  return fem_launch_apply_f32(op, x, y, nullptr, op->E, nullptr);
+}
+
+extern "C" fem_status fem_op_apply_elements(fem_op *op, const int32_t *elems, int64_t n,
+                                            const double *x, double *y) {
+  if (!op || !x || !y || x == y || n < 0 || (n > 0 && !elems)) {
+    fem_set_error("fem_op_apply_elements: invalid arguments");
+    return FEM_EINVAL;
+  }
+  FEM_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * op->N * op->ncomp, op->stream()));
+  return fem_launch_apply_f64(op, x, y, elems, n, nullptr);
+}
+
+extern "C" fem_status fem_op_diagonal(fem_op *op, double *d) {
+  if (!op || !d) { fem_set_error("fem_op_diagonal: invalid arguments"); return FEM_EINVAL; }
+  for (int c = 0; c < op->ncomp; c++)
+    FEM_CUDA_TRY(cudaMemcpyAsync(d + c * op->N, op->d_diag, sizeof(double) * op->N,
+                                 cudaMemcpyDeviceToDevice, op->stream()));
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_op_qdata_host(fem_op *op, int64_t e, double *out) {
+  if (!op || !out || e < 0 || e >= op->E) { fem_set_error("fem_op_qdata_host: invalid arguments"); return FEM_EINVAL; }
+  const int nd = op->kind == FEM_DIFFUSION ? 6 : 1;
+  const int64_t Q3 = (int64_t)op->Q * op->Q * op->Q;
+  FEM_CUDA_TRY(cudaMemcpyAsync(out, op->d_qdata + e * nd * Q3, sizeof(double) * nd * Q3,
+                               cudaMemcpyDeviceToHost, op->stream()));
+  FEM_CUDA_TRY(cudaStreamSynchronize(op->stream()));
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_op_rhs(fem_op *op, int which, double *b) {
+  if (!op || !b || (which != 0 && which != 1)) { fem_set_error("fem_op_rhs: invalid arguments"); return FEM_EINVAL; }
+  return fem_launch_rhs(op, which, b);
+}
+
+extern "C" fem_status fem_cg_solve(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
+                                   fem_cg_stats *st) {
+  if (!op || !b || !x || !o || b == x) { fem_set_error("fem_cg_solve: invalid arguments"); return FEM_EINVAL; }
+  if (o->precond != FEM_PC_NONE && o->precond != FEM_PC_JACOBI) {
+    fem_set_error("fem_cg_solve: preconditioner %d not available in plain CG", o->precond);
+    return FEM_EINVAL;
+  }
+  if (o->maxit < 0 || !(o->rtol >= 0.0)) { fem_set_error("fem_cg_solve: bad maxit/rtol"); return FEM_EINVAL; }
+  return fem_cg_run(op, b, x, o, st);
+}
+
+void fem_refine_free(fem_op *) {}

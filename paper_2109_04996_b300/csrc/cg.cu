@@ -1,0 +1,358 @@
+// Preconditioned conjugate gradients on the Dirichlet-constrained bake-off
+// systems (section "Benchmarks": CG iterations with their global reductions;
+// diagonal preconditioner as in Nekbone, section "Miniapps").
+//
+// Per iteration three kernels, all scalars resident on the device:
+//   apply      y = A p, with p^T A p summed in the same kernel (the element
+//              contributions p_e^T A_e p_e add up to p^T A p);
+//   update     alpha = rz / pAp; x += alpha p; r -= alpha y (interior only);
+//              z = r / diag (Jacobi) or z = r; r^T z and ||r||^2 by a
+//              deterministic grid reduction whose last block forms beta,
+//              counts the iteration and decides convergence;
+//   direction  p = z + beta p; y = 0 (ready for the next atomic apply).
+// With use_graph the loop is one CUDA graph: a conditional WHILE node whose
+// flag the update kernel's last block clears, so the host never sees a
+// scalar until the solve ends (the paper's Laghos note: one dot product per
+// iteration brought back to the CPU; here none is).
+#include <math.h>
+
+#include "fem_internal.h"
+
+struct CgWork {
+  int64_t n = 0;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *y = nullptr, *dinv = nullptr;
+  CgScalars *sc = nullptr;
+  double *partials = nullptr;
+  unsigned *counter = nullptr;
+  int dinv_pc = -1;          // preconditioner dinv currently holds
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const double *g_b = nullptr;
+  double *g_x = nullptr;
+};
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  if (g > 148 * 8) g = 148 * 8;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+__global__ void cg_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N, int64_t n,
+                               int pc, double *dinv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = i % N;
+    const bool fixed = dir && dir[node];
+    dinv[i] = fixed ? 0.0 : (pc == FEM_PC_JACOBI ? 1.0 / diag[node] : 1.0);
+  }
+}
+
+// x <- M x (Dirichlet entries to 0), y <- 0
+__global__ void cg_prepare_kernel(double *x, double *y, const uint8_t *dir, int64_t N,
+                                  int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (dir && dir[i % N]) x[i] = 0.0;
+    y[i] = 0.0;
+  }
+}
+
+struct CgParams {
+  const double *b;
+  double *x, *r, *z, *p, *y;
+  const double *dinv;
+  const uint8_t *dir;
+  int64_t N, n;
+  CgScalars *sc;
+  double *partials;
+  unsigned *counter;
+  cudaGraphConditionalHandle handle;
+  int use_graph;
+};
+
+__device__ void cg_set_continue(const CgParams &c, int cont) {
+  if (c.use_graph) cudaGraphSetConditional(c.handle, cont ? 1u : 0u);
+}
+
+// r = M (b - A x0); z = dinv r; p = z; y = 0; rz, rr, bb.
+__global__ void cg_init_kernel(const CgParams c) {
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool fixed = c.dir && c.dir[i % c.N];
+    const double bi = fixed ? 0.0 : c.b[i];
+    const double ri = fixed ? 0.0 : bi - c.y[i];
+    const double zi = c.dinv[i] * ri;
+    c.r[i] = ri; c.z[i] = zi; c.p[i] = zi; c.y[i] = 0.0;
+    v[0] += ri * zi; v[1] += ri * ri; v[2] += bi * bi;
+  }
+  __shared__ double tot[3];
+  if (fem_grid_sum<3>(v, c.partials, c.counter, tot) && threadIdx.x == 0) {
+    CgScalars *s = c.sc;
+    s->rz = tot[0]; s->rr = tot[1]; s->bb = tot[2];
+    s->tol2 = s->tol2 * tot[2];  // host stored rtol^2
+    s->iter = 0; s->pAp = 0.0; s->alpha = 0.0; s->beta = 0.0;
+    s->status = FEM_OK;
+    int done = 0;
+    if (!(tot[2] > 0.0)) done = 1;                       // b = 0: x = x0 (= 0 interior)
+    else if (s->tol2 > 0.0 && tot[1] <= s->tol2) done = 1;
+    else if (s->maxit <= 0) { done = 1; if (s->tol2 > 0.0) s->status = FEM_ENOCONV; }
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) { done = 1; s->status = FEM_EBREAKDOWN; }
+    s->done = done;
+    cg_set_continue(c, !done);
+  }
+}
+
+__global__ void cg_update_kernel(const CgParams c) {
+  CgScalars *s = c.sc;
+  if (s->done) return;  // host-driven loop ran past convergence
+  const double pAp = s->pAp;
+  const double alpha = s->rz / pAp;
+  const bool ok = (pAp > 0.0) && isfinite(alpha);
+  double v[2] = {0.0, 0.0};
+  if (ok) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double di = c.dinv[i];
+      const bool fixed = c.dir && c.dir[i % c.N];
+      double ri = c.r[i];
+      c.x[i] += alpha * c.p[i];
+      if (!fixed) ri -= alpha * c.y[i];
+      c.r[i] = ri;
+      const double zi = di * ri;
+      c.z[i] = zi;
+      v[0] += ri * zi; v[1] += ri * ri;
+    }
+  }
+  __shared__ double tot[2];
+  if (fem_grid_sum<2>(v, c.partials, c.counter, tot) && threadIdx.x == 0) {
+    int done = 0;
+    if (!ok) {
+      s->status = FEM_EBREAKDOWN; done = 1;
+    } else {
+      s->alpha = alpha;
+      s->beta = tot[0] / s->rz;
+      s->rz = tot[0]; s->rr = tot[1];
+      s->iter += 1;
+      if (!isfinite(tot[0]) || !isfinite(tot[1])) { s->status = FEM_EBREAKDOWN; done = 1; }
+      else if (s->tol2 > 0.0 && tot[1] <= s->tol2) done = 1;
+      else if (s->iter >= s->maxit) { done = 1; if (s->tol2 > 0.0) s->status = FEM_ENOCONV; }
+    }
+    s->done = done;
+    cg_set_continue(c, !done);
+  }
+}
+
+__global__ void cg_direction_kernel(const CgParams c) {
+  const double beta = c.sc->beta;
+  if (c.sc->done && !c.use_graph) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    c.p[i] = c.z[i] + beta * c.p[i];
+    c.y[i] = 0.0;
+  }
+}
+
+int ensure_work(fem_op *op) {
+  if (op->cg) return FEM_OK;
+  CgWork *w = new CgWork();
+  op->cg = w;
+  w->n = op->N * op->ncomp;
+  const size_t vb = sizeof(double) * (size_t)w->n;
+  if (cudaMalloc(&w->r, vb) != cudaSuccess || cudaMalloc(&w->z, vb) != cudaSuccess ||
+      cudaMalloc(&w->p, vb) != cudaSuccess || cudaMalloc(&w->y, vb) != cudaSuccess ||
+      cudaMalloc(&w->dinv, vb) != cudaSuccess || cudaMalloc(&w->sc, sizeof(CgScalars)) != cudaSuccess ||
+      cudaMalloc(&w->partials, sizeof(double) * 4 * FEM_MAX_BLOCKS) != cudaSuccess ||
+      cudaMalloc(&w->counter, sizeof(unsigned) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    fem_set_error("fem_cg_solve: device allocation of the CG workspace failed");
+    return FEM_ENOMEM;
+  }
+  FEM_CUDA_TRY(cudaMemsetAsync(w->counter, 0, sizeof(unsigned) * 4, op->stream()));
+  op->bytes += 5 * vb;
+  return FEM_OK;
+}
+
+CgParams make_params(fem_op *op, const double *b, double *x, cudaGraphConditionalHandle h,
+                     int use_graph) {
+  CgWork *w = op->cg;
+  CgParams c;
+  c.b = b; c.x = x; c.r = w->r; c.z = w->z; c.p = w->p; c.y = w->y; c.dinv = w->dinv;
+  c.dir = op->mesh->d_dirichlet; c.N = op->N; c.n = w->n; c.sc = w->sc;
+  c.partials = w->partials; c.counter = w->counter; c.handle = h; c.use_graph = use_graph;
+  return c;
+}
+
+// The launches of one solve before the loop.
+int launch_prologue(fem_op *op, const CgParams &c, cudaStream_t s) {
+  const int g = grid_for(c.n);
+  cg_prepare_kernel<<<g, kThreads, 0, s>>>(c.x, c.y, c.dir, c.N, c.n);
+  FEM_CHECK_LAUNCH();
+  // the apply launcher uses the operator's stream; route it to s
+  int rc = fem_launch_apply_f64(op, c.x, c.y, nullptr, op->E, nullptr);
+  if (rc) return rc;
+  cg_init_kernel<<<g, kThreads, 0, s>>>(c);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
+int launch_body(fem_op *op, const CgParams &c, cudaStream_t s) {
+  const int g = grid_for(c.n);
+  int rc = fem_launch_apply_f64(op, c.p, c.y, nullptr, op->E, &c.sc->pAp);
+  if (rc) return rc;
+  cg_update_kernel<<<g, kThreads, 0, s>>>(c);
+  FEM_CHECK_LAUNCH();
+  cg_direction_kernel<<<g, kThreads, 0, s>>>(c);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
+void destroy_graph(CgWork *w) {
+  if (w->exec) cudaGraphExecDestroy(w->exec);
+  if (w->graph) cudaGraphDestroy(w->graph);
+  w->exec = nullptr; w->graph = nullptr;
+}
+
+}  // namespace
+
+// Streams used while capturing: the apply launcher enqueues on
+// op->stream(), so capture happens on the operator's own stream (mesh stream
+// swapped for the duration of the capture).
+static int build_graph(fem_op *op, const double *b, double *x) {
+  CgWork *w = op->cg;
+  destroy_graph(w);
+  fem_mesh *mesh = const_cast<fem_mesh *>(op->mesh);
+  cudaStream_t user = mesh->stream;
+  if (!w->cap) {
+    FEM_CUDA_TRY(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+    FEM_CUDA_TRY(cudaStreamCreateWithFlags(&w->cap2, cudaStreamNonBlocking));
+  }
+  int rc = FEM_OK;
+  cudaGraph_t graph = nullptr;
+  mesh->stream = w->cap;
+  FEM_CUDA_TRY(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeRelaxed));
+  {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cnode;
+    cudaGraph_t body;
+    CgParams c;
+    cudaError_t e = cudaStreamGetCaptureInfo(w->cap, &st, nullptr, &graph, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
+    c = make_params(op, b, x, h, 1);
+    rc = launch_prologue(op, c, w->cap);
+    if (rc) goto end_capture;
+    e = cudaStreamGetCaptureInfo(w->cap, &st, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
+    body = cp.conditional.phGraph_out[0];
+    e = cudaStreamUpdateCaptureDependencies(w->cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
+    mesh->stream = w->cap2;
+    e = cudaStreamBeginCaptureToGraph(w->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
+    rc = launch_body(op, c, w->cap2);
+    {
+      cudaGraph_t tmp;
+      cudaError_t e2 = cudaStreamEndCapture(w->cap2, &tmp);
+      if (!rc && e2 != cudaSuccess) rc = FEM_ECUDA;
+    }
+    mesh->stream = w->cap;
+  }
+end_capture : {
+  cudaGraph_t g2 = nullptr;
+  cudaError_t e = cudaStreamEndCapture(w->cap, &g2);
+  mesh->stream = user;
+  if (rc == FEM_OK && e != cudaSuccess) rc = FEM_ECUDA;
+  if (rc != FEM_OK) {
+    if (g2) cudaGraphDestroy(g2);
+    cudaGetLastError();
+    if (rc == FEM_ECUDA) fem_set_error("fem_cg_solve: building the CUDA graph failed: %s", cudaGetErrorString(e));
+    return rc;
+  }
+  w->graph = g2;
+}
+  FEM_CUDA_TRY(cudaGraphInstantiate(&w->exec, w->graph, 0));
+  w->g_b = b; w->g_x = x;
+  return FEM_OK;
+}
+
+int fem_cg_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
+               fem_cg_stats *st) {
+  int rc = ensure_work(op);
+  if (rc) return rc;
+  CgWork *w = op->cg;
+  cudaStream_t s = op->stream();
+  if (w->dinv_pc != o->precond) {
+    cg_dinv_kernel<<<grid_for(w->n), kThreads, 0, s>>>(op->d_diag, op->mesh->d_dirichlet, op->N,
+                                                       w->n, o->precond, w->dinv);
+    FEM_CHECK_LAUNCH();
+    w->dinv_pc = o->precond;
+  }
+  CgScalars init = {};
+  init.maxit = o->maxit;
+  init.tol2 = o->rtol * o->rtol;
+  FEM_CUDA_TRY(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  if (o->use_graph) {
+    if (!w->exec || w->g_b != b || w->g_x != x) {
+      // the capture streams must see the work queued so far on s
+      FEM_CUDA_TRY(cudaStreamSynchronize(s));
+      rc = build_graph(op, b, x);
+      if (rc) return rc;
+    }
+    FEM_CUDA_TRY(cudaGraphLaunch(w->exec, s));
+  } else {
+    CgParams c = make_params(op, b, x, 0, 0);
+    rc = launch_prologue(op, c, s);
+    if (rc) return rc;
+    for (int it = 0; it < o->maxit; it++) {
+      rc = launch_body(op, c, s);
+      if (rc) return rc;
+      if ((it & 7) == 7 || it == o->maxit - 1) {
+        int done = 0;
+        FEM_CUDA_TRY(cudaMemcpyAsync(&done, &w->sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (done) break;
+      }
+    }
+  }
+  CgScalars out;
+  FEM_CUDA_TRY(cudaMemcpyAsync(&out, w->sc, sizeof(out), cudaMemcpyDeviceToHost, s));
+  FEM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st) {
+    st->iterations = out.iter;
+    st->outer = 0;
+    st->status = out.status;
+    st->rnorm = sqrt(out.rr);
+    st->bnorm = sqrt(out.bb);
+    st->true_rel = -1.0;
+  }
+  return out.status;
+}
+
+void fem_cg_free(fem_op *op) {
+  CgWork *w = op->cg;
+  if (!w) return;
+  destroy_graph(w);
+  if (w->cap) cudaStreamDestroy(w->cap);
+  if (w->cap2) cudaStreamDestroy(w->cap2);
+  cudaFree(w->r); cudaFree(w->z); cudaFree(w->p); cudaFree(w->y); cudaFree(w->dinv);
+  cudaFree(w->sc); cudaFree(w->partials); cudaFree(w->counter);
+  delete w;
+  op->cg = nullptr;
+}

@@ -1,0 +1,186 @@
+// Internal declarations of the FEM library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fem.h"
+
+#define FEM_MAX_P 9    // P = p + 1 <= 9
+#define FEM_MAX_Q 10   // q <= p + 2 <= 10
+
+// Thread-local error message, set by every failing entry point.
+void fem_set_error(const char *fmt, ...);
+
+#define FEM_CUDA_TRY(call)                                                   \
+  do {                                                                       \
+    cudaError_t err_ = (call);                                               \
+    if (err_ != cudaSuccess) {                                               \
+      fem_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(err_), \
+                    __FILE__, __LINE__);                                     \
+      return FEM_ECUDA;                                                      \
+    }                                                                        \
+  } while (0)
+
+#define FEM_CHECK_LAUNCH()                                                   \
+  do {                                                                       \
+    cudaError_t err_ = cudaGetLastError();                                   \
+    if (err_ != cudaSuccess) {                                               \
+      fem_set_error("kernel launch failed: %s (%s:%d)",                      \
+                    cudaGetErrorString(err_), __FILE__, __LINE__);           \
+      return FEM_ECUDA;                                                      \
+    }                                                                        \
+  } while (0)
+
+// 1D tables of one operator, host FP64 (basis.cu).
+struct BasisTables {
+  int p, P, q, quad;
+  double z[FEM_MAX_P];                    // Gauss-Lobatto nodes of the basis
+  double r[FEM_MAX_Q], w[FEM_MAX_Q];      // quadrature points / weights
+  double B[FEM_MAX_Q * FEM_MAX_P];        // l_a(r_k)          [k][a]
+  double G[FEM_MAX_Q * FEM_MAX_P];        // l_a'(r_k)         [k][a]
+  double Dq[FEM_MAX_Q * FEM_MAX_Q];       // derivative of the Lagrange basis
+                                          // on the quadrature points, at them
+};
+int fem_build_tables(int p, int q, int quad, BasisTables *t);
+
+// Scalars of one CG run, resident on the device.
+struct CgScalars {
+  double rz;       // r^T z of the current iterate
+  double rz_new;
+  double pAp;      // fused into the apply
+  double rr;       // ||r||^2
+  double bb;       // ||b||^2 (constrained)
+  double alpha, beta;
+  double tol2;     // rtol^2 * bb
+  int iter, maxit;
+  int status;      // FEM_OK / FEM_ENOCONV / FEM_EBREAKDOWN
+  int done;
+};
+
+struct fem_mesh {
+  int p, P;
+  int64_t N, E;
+  int32_t *d_elem_nodes = nullptr;  // [E][P^3]
+  double *d_xyz = nullptr;          // [3][N] (SoA)
+  uint8_t *d_dirichlet = nullptr;   // [N], 1 = constrained
+  cudaStream_t stream = nullptr;
+  int64_t bytes = 0;
+};
+
+struct CgWork;
+struct RefineWork;
+
+struct fem_op {
+  const fem_mesh *mesh = nullptr;
+  int kind, quad, q, ncomp, prec;
+  int P, Q;
+  bool colloc;                    // Gauss-Lobatto with q = p+1: B = identity
+  int64_t N, E;
+  BasisTables tab;
+  double *d_B = nullptr, *d_Dq = nullptr;   // device copies of B [Q][P], Dq [Q][Q]
+  float *d_B32 = nullptr, *d_Dq32 = nullptr;
+  double *d_qdata = nullptr;      // [E][nd][Q^3]
+  float *d_qdata32 = nullptr;     // FP32 copy (prec == FEM_F32)
+  double *d_diag = nullptr;       // [N] scalar diagonal
+  double *d_rff = nullptr;        // [M][4]
+  int M = 0;
+  double sigma = 1.0;
+  // reduction scratch for the fused dot products
+  double *d_partials = nullptr;   // [FEM_MAX_BLOCKS * 4]
+  unsigned *d_counter = nullptr;  // [4]
+  int64_t bytes = 0;
+  CgWork *cg = nullptr;
+  RefineWork *ir = nullptr;
+  cudaStream_t stream() const { return mesh->stream; }
+};
+
+#define FEM_MAX_BLOCKS 8192
+
+// Device table block of an operator: B [Q][P] | Dq [Q][Q] | G [Q][P] | w [Q]
+// at fixed offsets (FP64 and FP32 copies).
+#define TAB_B 0
+#define TAB_DQ (FEM_MAX_Q * FEM_MAX_P)
+#define TAB_G (TAB_DQ + FEM_MAX_Q * FEM_MAX_Q)
+#define TAB_W (TAB_G + FEM_MAX_Q * FEM_MAX_P)
+#define TAB_SIZE (TAB_W + FEM_MAX_Q)
+
+// ---- launchers (apply.cu)
+int fem_launch_apply_f64(fem_op *op, const double *x, double *y,
+                         const int32_t *list, int64_t nsel, double *dot_out);
+int fem_launch_apply_f32(fem_op *op, const float *x, float *y,
+                         const int32_t *list, int64_t nsel, double *dot_out);
+// ---- setup (setup.cu)
+int fem_setup_qdata(fem_op *op);
+int fem_setup_diagonal(fem_op *op);
+int fem_launch_rhs(fem_op *op, int which, double *b);
+// ---- CG (cg.cu)
+int fem_cg_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
+               fem_cg_stats *st);
+void fem_cg_free(fem_op *op);
+
+// ---------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+__device__ __forceinline__ double fem_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic grid-wide sum of NV doubles per thread.  Every block writes
+// its partial sums; the last block to arrive (ticket counter) adds the
+// partials in block order and leaves the totals in `tot` (shared, valid in
+// the last block only) and resets the counter.  Returns true in the last
+// block.  blockDim.x must be a multiple of 32.  No block waits on another.
+template <int NV>
+__device__ bool fem_grid_sum(const double (&v)[NV], double *partials,
+                             unsigned *counter, double (&tot)[NV]) {
+  __shared__ double red[NV][32];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    double s = fem_warp_sum(v[k]);
+    if (lane == 0) red[k][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      double s = lane < nwarps ? red[k][lane] : 0.0;
+      s = fem_warp_sum(s);
+      if (lane == 0) partials[(size_t)k * FEM_MAX_BLOCKS + blockIdx.x] = s;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned ticket = atomicAdd(counter, 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; k++) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s += ((volatile double *)partials)[(size_t)k * FEM_MAX_BLOCKS + b];
+    s = fem_warp_sum(s);
+    if (lane == 0) red[k][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      double s = 0.0;
+      for (int w = 0; w < nwarps; w++) s += red[k][w];
+      tot[k] = s;
+    }
+    *counter = 0u;
+  }
+  __syncthreads();
+  return true;
+}
+#endif
