@@ -200,6 +200,34 @@ typedef struct {
 fem_status fem_cg_solve(fem_op *op, const double *b, double *x,
                         const fem_cg_opts *opts, fem_cg_stats *stats);
 
+/* ------------------------------------------------------- allocation-free solve */
+
+/* Largest ncomp*N accepted by fem_cg_solve_noalloc. */
+#define FEM_NOALLOC_MAX_N 131072
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory while they solve: code that works inside
+ * a device-memory budget fixed at start-up, or a real-time loop in which
+ * cudaMalloc's implicit device-wide synchronization is not acceptable.
+ *
+ * Same arguments, arithmetic and results as fem_cg_solve (FEM_PC_NONE or
+ * FEM_PC_JACOBI; launches are host-driven, no CUDA graph), but the CG
+ * workspace (five vectors, reduction partials, scalars) lives in one fixed
+ * file-scope device array of the library instead of cudaMalloc'd buffers, so
+ * the call allocates nothing.  The array holds 5 * FEM_NOALLOC_MAX_N doubles
+ * plus about 260 KB and is held on every GPU that loads the library until the
+ * process exits.
+ *  - ncomp*N > FEM_NOALLOC_MAX_N: FEM_EINVAL with a message naming the limit.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call shares the array and it keeps the previous call's contents;
+ *    each call rewrites what it reads first.  Calls that overlap on the GPU
+ *    (other streams, other host threads) race on it and give wrong results.
+ *  - The operator itself was allocated by fem_op_create; b and x are the
+ *    caller's device buffers.  Synchronizes the operator's stream. */
+fem_status fem_cg_solve_noalloc(fem_op *op, const double *b, double *x,
+                                const fem_cg_opts *opts, fem_cg_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -356,3 +356,129 @@ void fem_cg_free(fem_op *op) {
   delete w;
   op->cg = nullptr;
 }
+
+// ---------------------------------------------------------------------------
+// fem_cg_solve_noalloc: the same Jacobi/plain CG as fem_cg_solve, for callers
+// that must not allocate device memory while solving (a fixed memory budget
+// handed out once at start-up, a real-time loop where cudaMalloc's implicit
+// device-wide synchronization is not acceptable).  Its workspace is one
+// file-scope device array of fixed size instead of cudaMalloc'd buffers.
+//
+// Layout of the array: 5 vectors r, z, p, y, dinv of FEM_NOALLOC_MAX_N
+// doubles each, the grid-reduction partials, the CG scalars and the ticket
+// counters.  Every GPU that loads the library holds it until the process
+// exits.  All calls share it and it keeps the last call's contents; each call
+// rewrites every part it reads before reading it.  Calls that overlap on the
+// GPU (two streams, two host threads) race on it.
+namespace {
+
+constexpr size_t kNaVec = (size_t)FEM_NOALLOC_MAX_N * sizeof(double);
+constexpr size_t kNaPart = (size_t)4 * FEM_MAX_BLOCKS * sizeof(double);
+constexpr size_t kNaScal = ((sizeof(CgScalars) + 255) / 256) * 256;
+constexpr size_t kNaBytes = 5 * kNaVec + kNaPart + kNaScal + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char *g_noalloc_base[kMaxDevices] = {nullptr};
+
+// Device address of the array on the current device, looked up once per
+// device (host code cannot use the symbol's name as a device address).
+int noalloc_base(unsigned char **out) {
+  int dev = 0;
+  FEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    fem_set_error("fem_cg_solve_noalloc: device %d beyond the %d supported", dev, kMaxDevices);
+    return FEM_EINVAL;
+  }
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      fem_set_error("fem_cg_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return FEM_ECUDA;
+    }
+    g_noalloc_base[dev] = (unsigned char *)p;
+  }
+  *out = g_noalloc_base[dev];
+  return FEM_OK;
+}
+
+__global__ void cg_noalloc_reset_kernel(CgScalars *sc, unsigned *counter, int maxit, double tol2) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    CgScalars s = {};
+    s.maxit = maxit;
+    s.tol2 = tol2;
+    *sc = s;
+    for (int i = 0; i < 4; i++) counter[i] = 0u;
+  }
+}
+
+}  // namespace
+
+extern "C" fem_status fem_cg_solve_noalloc(fem_op *op, const double *b, double *x,
+                                           const fem_cg_opts *o, fem_cg_stats *st) {
+  if (!op || !b || !x || !o || b == x) {
+    fem_set_error("fem_cg_solve_noalloc: invalid arguments");
+    return FEM_EINVAL;
+  }
+  if (o->precond != FEM_PC_NONE && o->precond != FEM_PC_JACOBI) {
+    fem_set_error("fem_cg_solve_noalloc: preconditioner %d not available", o->precond);
+    return FEM_EINVAL;
+  }
+  if (o->maxit < 0 || !(o->rtol >= 0.0)) {
+    fem_set_error("fem_cg_solve_noalloc: bad maxit/rtol");
+    return FEM_EINVAL;
+  }
+  const int64_t n = op->N * op->ncomp;
+  if (n > FEM_NOALLOC_MAX_N) {
+    fem_set_error("fem_cg_solve_noalloc: ncomp*N = %lld exceeds the fixed workspace of %d entries",
+                  (long long)n, FEM_NOALLOC_MAX_N);
+    return FEM_EINVAL;
+  }
+  unsigned char *base = nullptr;
+  int rc = noalloc_base(&base);
+  if (rc) return rc;
+  double *vec = (double *)base;
+  double *partials = (double *)(base + 5 * kNaVec);
+  CgScalars *sc = (CgScalars *)(base + 5 * kNaVec + kNaPart);
+  unsigned *counter = (unsigned *)(base + 5 * kNaVec + kNaPart + kNaScal);
+  cudaStream_t s = op->stream();
+  cg_noalloc_reset_kernel<<<1, 32, 0, s>>>(sc, counter, o->maxit, o->rtol * o->rtol);
+  FEM_CHECK_LAUNCH();
+  CgParams c;
+  c.b = b; c.x = x;
+  c.r = vec; c.z = vec + FEM_NOALLOC_MAX_N; c.p = vec + 2 * (size_t)FEM_NOALLOC_MAX_N;
+  c.y = vec + 3 * (size_t)FEM_NOALLOC_MAX_N;
+  double *dinv = vec + 4 * (size_t)FEM_NOALLOC_MAX_N;
+  c.dinv = dinv;
+  c.dir = op->mesh->d_dirichlet; c.N = op->N; c.n = n; c.sc = sc;
+  c.partials = partials; c.counter = counter; c.handle = 0; c.use_graph = 0;
+  cg_dinv_kernel<<<grid_for(n), kThreads, 0, s>>>(op->d_diag, op->mesh->d_dirichlet, op->N, n,
+                                                  o->precond, dinv);
+  FEM_CHECK_LAUNCH();
+  rc = launch_prologue(op, c, s);
+  if (rc) return rc;
+  for (int it = 0; it < o->maxit; it++) {
+    rc = launch_body(op, c, s);
+    if (rc) return rc;
+    if ((it & 7) == 7 || it == o->maxit - 1) {
+      int done = 0;
+      FEM_CUDA_TRY(cudaMemcpyAsync(&done, &sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FEM_CUDA_TRY(cudaStreamSynchronize(s));
+      if (done) break;
+    }
+  }
+  CgScalars out;
+  FEM_CUDA_TRY(cudaMemcpyAsync(&out, sc, sizeof(out), cudaMemcpyDeviceToHost, s));
+  FEM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st) {
+    st->iterations = out.iter;
+    st->outer = 0;
+    st->status = out.status;
+    st->rnorm = sqrt(out.rr);
+    st->bnorm = sqrt(out.bb);
+    st->true_rel = -1.0;
+  }
+  return out.status;
+}
