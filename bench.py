@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--iters", type=int, default=10, help="CG iterations per order per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven CG loop (same kernels; for profilers)")
+    ap.add_argument("--tts-dofs", type=float, default=1e7,
+                    help="size of the time-to-1e-10 comparison (0 = skip)")
+    ap.add_argument("--tts-order", type=int, default=4)
     return ap.parse_args()
 
 
@@ -185,6 +190,44 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def time_to_solution(fem, torch, args):
+    """BP3 at one order: wall time to ||b - A x|| <= 1e-10 ||b|| (true FP64
+    residual) for plain FP64 Jacobi-PCG and for FP32 inner PCG + FP64
+    iterative refinement, same mesh, same right-hand side, same GPU."""
+    p = args.tts_order
+    n = fem_inputs.bp3_mesh_n(args.tts_dofs, p)
+    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=300 + p)
+    gm = fem.Mesh(m)
+    op = fem.Operator.bake_off(gm, "BP3", prec=fem.F32)
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=400 + p)).cuda()
+    out = {"problem": "BP3 p=%d n=%d N=%d" % (p, n, m["N"]), "rtol": 1e-10}
+    del m
+    res = {}
+    for name in ("fp64_pcg", "fp32_refined"):
+        best = None
+        for rep in range(2):  # first run builds the graphs
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "fp64_pcg":
+                st = op.cg(b, x, precond=fem.PC_JACOBI, rtol=1e-10, maxit=100000)
+            else:
+                st = op.solve_refined(b, x, rtol=1e-10, inner_rtol=1e-5)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            best = t if best is None else min(best, t)
+        # true FP64 residual of the returned x, by the FP64 apply
+        y = op.apply(x)
+        r = (b - y)
+        r[torch.from_numpy(gm.dirichlet.astype(bool)).cuda()] = 0.0
+        true_rel = (torch.linalg.norm(r) / torch.linalg.norm(b)).item()
+        res[name] = {"seconds": best, "iterations": st["iterations"], "outer": st["outer"],
+                     "status": st["status"], "true_rel_residual": true_rel}
+    res["speedup_refined_vs_fp64"] = res["fp64_pcg"]["seconds"] / res["fp32_refined"]["seconds"]
+    out.update(res)
+    return out
+
+
 def config(args, work):
     return {"workload": "BP3 FP64 Jacobi-PCG, Gauss-Legendre q=p+2, perturbed unit-cube "
                         "brick meshes of about %.0e DOFs per order" % args.dofs,
@@ -227,7 +270,8 @@ def main():
     def step():
         for p, n, gm, op, b, x in ops:
             x.zero_()
-            st = op.cg(b, x, precond=fem.PC_JACOBI, maxit=args.iters, rtol=0.0, use_graph=True)
+            st = op.cg(b, x, precond=fem.PC_JACOBI, maxit=args.iters, rtol=0.0,
+                       use_graph=not args.no_graph)
             assert st["iterations"] == args.iters, st
 
     for _ in range(args.warmup):
@@ -315,6 +359,9 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
             "gpu_launches": len(ops) * (3 + 3 * args.iters) * args.steps,
             "roofline": roofline, "clocks": clocks, "per_order": per_p}
+    del ops
+    if args.tts_dofs > 0:
+        line["time_to_solution"] = time_to_solution(fem, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(work, args.iters, args.cpu_seconds)
     if rank == 0:

@@ -200,6 +200,20 @@ typedef struct {
 fem_status fem_cg_solve(fem_op *op, const double *b, double *x,
                         const fem_cg_opts *opts, fem_cg_stats *stats);
 
+/* Mixed-precision solve of the same constrained system: FP64 iterative
+ * refinement (classical; the paper fixes only the operator and CG) around an
+ * inner Jacobi-PCG (or plain CG) that runs the FP32 apply on FP32 vectors
+ * with FP64 dot products and scalars.  Outer step: r = b - A_64 x (FP64
+ * apply); stop when ||r|| <= rtol ||b||; else solve A_32 d = r to
+ * inner_rtol (at most maxit inner iterations) and set x += d.  The operator
+ * must have been created with FEM_F32.  Each outer step is one CUDA graph
+ * launch; the host reads one status word per step (synchronizes).
+ * stats: iterations = inner iterations in total, outer = corrections,
+ * true_rel = ||b - A_64 x|| / ||b|| of the returned x.  Returns FEM_OK,
+ * FEM_ENOCONV (max_outer reached) or FEM_EBREAKDOWN. */
+fem_status fem_solve_refined(fem_op *op, const double *b, double *x,
+                             const fem_cg_opts *opts, fem_cg_stats *stats);
+
 /* ------------------------------------------------------- allocation-free solve */
 
 /* Largest ncomp*N accepted by fem_cg_solve_noalloc. */

@@ -78,6 +78,7 @@ def lib():
         "fem_op_qdata_host": [_VP, _I64, _VP],
         "fem_op_rhs": [_VP, ctypes.c_int, _VP],
         "fem_cg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
+        "fem_solve_refined": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -236,5 +237,20 @@ class Operator:
         rc = lib().fem_cg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
         if rc not in (0, 5):
             _check(rc)
-        return dict(iterations=st.iterations, outer=st.outer, status=STATUS[st.status],
-                    rnorm=st.rnorm, bnorm=st.bnorm, true_rel=st.true_rel)
+        return _stats(st)
+
+    def solve_refined(self, b, x, rtol=1e-10, inner_rtol=1e-5, maxit=100000, max_outer=20,
+                      precond=PC_JACOBI):
+        """FP64 iterative refinement around an FP32 inner PCG (operator
+        created with prec=F32).  x: initial guess in, solution out."""
+        o = _CgOpts(precond, int(maxit), float(rtol), 1, float(inner_rtol), int(max_outer))
+        st = _CgStats()
+        rc = lib().fem_solve_refined(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        if rc not in (0, 5):
+            _check(rc)
+        return _stats(st)
+
+
+def _stats(st):
+    return dict(iterations=st.iterations, outer=st.outer, status=STATUS[st.status],
+                rnorm=st.rnorm, bnorm=st.bnorm, true_rel=st.true_rel)

@@ -159,7 +159,6 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
 extern "C" fem_status fem_op_destroy(fem_op *op) {
   if (!op) return FEM_OK;
   fem_cg_free(op);
-  extern void fem_refine_free(fem_op *);
   fem_refine_free(op);
   if (op->d_B) cudaFree(op->d_B - TAB_B);
   if (op->d_B32) cudaFree(op->d_B32 - TAB_B);
@@ -237,4 +236,3 @@ extern "C" fem_status fem_cg_solve(fem_op *op, const double *b, double *x, const
   return fem_cg_run(op, b, x, o, st);
 }
 
-void fem_refine_free(fem_op *) {}

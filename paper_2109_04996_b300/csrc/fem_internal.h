@@ -119,6 +119,8 @@ int fem_launch_rhs(fem_op *op, int which, double *b);
 int fem_cg_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
                fem_cg_stats *st);
 void fem_cg_free(fem_op *op);
+// ---- mixed precision (refine.cu)
+void fem_refine_free(fem_op *op);
 
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__
