@@ -167,6 +167,37 @@ fem_status fem_op_qdata_host(fem_op *op, int64_t e, double *out_host);
  * b: device [N] (scalar). */
 fem_status fem_op_rhs(fem_op *op, int which, double *b);
 
+/* ---------------------------------------------------------------- autotuning */
+
+/* Launch shape of the fused apply: elements per block (a choice index:
+ * 0 = about 256 threads per block, 1 = half that, 2 = twice that; only
+ * diffusion operators with q = p+2 Gauss or collocated Lobatto have choices
+ * 1 and 2) and resident blocks per SM (0 = the occupancy maximum). */
+typedef struct {
+  int epb_choice;
+  int blocks_per_sm;
+  double us;          /* measured time of one apply of this operator, us */
+  int from_cache;     /* 1 if read from the cache file, 0 if timed now */
+  int candidates;     /* shapes timed */
+} fem_tune_result;
+
+/* Set the launch shape used by this operator's apply of precision prec
+ * (FEM_F64 or FEM_F32).  Every shape computes the same result up to the
+ * order of the atomic additions.  FEM_EINVAL for an invalid choice. */
+fem_status fem_op_set_launch_shape(fem_op *op, int prec, int epb_choice,
+                                   int blocks_per_sm);
+
+/* Autotuner (the paper specializes kernels on the order by just-in-time
+ * compilation, sections "Ecosystem" and "libCEED"; here the variants are
+ * precompiled and timed): time every valid launch shape of the apply of
+ * precision prec on this operator's mesh with CUDA events (2 warm-up + 5
+ * timed launches each), keep the fastest for the operator.  cache_path: NULL,
+ * or a JSON file keyed by (GPU architecture, P, q, kind, collocation, ncomp,
+ * precision, log2 E); a hit skips the timing, a miss adds the entry.
+ * Allocates two temporary vectors; synchronizes. */
+fem_status fem_op_autotune(fem_op *op, int prec, const char *cache_path,
+                           fem_tune_result *result);
+
 /* ---------------------------------------------------------------- solvers */
 
 typedef struct {
@@ -213,6 +244,55 @@ fem_status fem_cg_solve(fem_op *op, const double *b, double *x,
  * FEM_ENOCONV (max_outer reached) or FEM_EBREAKDOWN. */
 fem_status fem_solve_refined(fem_op *op, const double *b, double *x,
                              const fem_cg_opts *opts, fem_cg_stats *stats);
+
+/* ---------------------------------------------------------------- batches */
+
+typedef struct fem_batch fem_batch;
+
+/* A batch of independent problems solved together (no counterpart in the
+ * paper beyond batching small products across elements, section
+ * "Ecosystem").  ops: n operators (1 <= n <= 1024), each a diffusion
+ * operator with Gauss q = p+2 (BP3/BP4 type, any order and size) created
+ * with FEM_F32, all on one stream.  The batch keeps pointers to the
+ * operators (they must outlive it) and allocates the per-problem inner
+ * vectors. */
+fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **out);
+fem_status fem_batch_destroy(fem_batch *batch);
+
+/* Solve every problem i: (M A_i M + (I - M)) x_i = b_i with the method of
+ * fem_solve_refined (FP64 refinement, FP32 inner Jacobi-PCG, FP64 dots), all
+ * problems in lockstep outer steps; the inner iterations of all problems of
+ * one outer step run in ONE persistent cooperative kernel (work items:
+ * (problem, element group) and (problem, vector chunk); grid barriers with a
+ * wall-clock limit).  b, x: host arrays of n device pointers.  opts: precond
+ * must be FEM_PC_JACOBI; rtol, inner_rtol, maxit (inner cap per step),
+ * max_outer as in fem_solve_refined.  stats: host array of n (or NULL).
+ * Returns the first non-OK problem status, or FEM_ETIMEOUT if a barrier ran
+ * out (the batch stays usable).  Synchronizes. */
+fem_status fem_batch_solve(fem_batch *batch, const double *const *b,
+                           double *const *x, const fem_cg_opts *opts,
+                           fem_cg_stats *stats);
+
+/* Launch shape of the persistent kernel: block size choice (0: 128, 1: 256,
+ * 2: 512 threads), blocks per SM (0 = occupancy maximum) and the barrier
+ * wall-clock limit in ms. */
+fem_status fem_batch_set_shape(fem_batch *batch, int nt_choice,
+                               int blocks_per_sm, double timeout_ms);
+
+/* Autotuner of the batch: time `iters` inner iterations of the persistent
+ * kernel for every (block size, blocks per SM) candidate from the same start
+ * state (b, x as in fem_batch_solve; x is not modified), keep the fastest.
+ * result->epb_choice holds the block size choice, result->us the time of one
+ * inner iteration of the whole batch. */
+fem_status fem_batch_autotune(fem_batch *batch, const double *const *b,
+                              double *const *x, int iters,
+                              fem_tune_result *result);
+
+/* Self-test of the bounded grid barrier: launches the persistent kernel with
+ * one arrival that never comes; the first barrier runs out after timeout_ms
+ * and the call returns FEM_ETIMEOUT with the batch still usable.  Requires a
+ * previous fem_batch_solve (it reuses the bound vectors). */
+fem_status fem_batch_barrier_selftest(fem_batch *batch, double timeout_ms);
 
 /* ------------------------------------------------------- allocation-free solve */
 

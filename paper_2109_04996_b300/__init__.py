@@ -36,6 +36,12 @@ class FemError(RuntimeError):
         self.code = code
 
 
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("epb_choice", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("us", ctypes.c_double), ("from_cache", ctypes.c_int),
+                ("candidates", ctypes.c_int)]
+
+
 class _CgOpts(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("use_graph", ctypes.c_int), ("inner_rtol", ctypes.c_double),
@@ -79,6 +85,16 @@ def lib():
         "fem_op_rhs": [_VP, ctypes.c_int, _VP],
         "fem_cg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_solve_refined": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
+        "fem_op_set_launch_shape": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+        "fem_op_autotune": [_VP, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(_TuneResult)],
+        "fem_batch_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
+        "fem_batch_destroy": [_VP],
+        "fem_batch_solve": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                            ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
+        "fem_batch_set_shape": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double],
+        "fem_batch_autotune": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
+                               ctypes.POINTER(_TuneResult)],
+        "fem_batch_barrier_selftest": [_VP, ctypes.c_double],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -239,6 +255,18 @@ class Operator:
             _check(rc)
         return _stats(st)
 
+    def set_launch_shape(self, prec, epb_choice, blocks_per_sm=0):
+        _check(lib().fem_op_set_launch_shape(self._h, prec, epb_choice, blocks_per_sm))
+
+    def autotune(self, prec=F64, cache=None):
+        """Time the apply's launch shapes and keep the fastest (see
+        fem_op_autotune).  Returns the chosen shape as a dict."""
+        r = _TuneResult()
+        _check(lib().fem_op_autotune(self._h, prec, None if cache is None else cache.encode(),
+                                     ctypes.byref(r)))
+        return dict(epb_choice=r.epb_choice, blocks_per_sm=r.blocks_per_sm, us=r.us,
+                    from_cache=bool(r.from_cache), candidates=r.candidates)
+
     def solve_refined(self, b, x, rtol=1e-10, inner_rtol=1e-5, maxit=100000, max_outer=20,
                       precond=PC_JACOBI):
         """FP64 iterative refinement around an FP32 inner PCG (operator
@@ -254,3 +282,49 @@ class Operator:
 def _stats(st):
     return dict(iterations=st.iterations, outer=st.outer, status=STATUS[st.status],
                 rnorm=st.rnorm, bnorm=st.bnorm, true_rel=st.true_rel)
+
+
+class Batch:
+    """Independent BP3/BP4-type problems (FP32 operators, Gauss q = p+2)
+    solved together: FP64 refinement, the inner FP32 PCG of all problems in
+    one persistent kernel per outer step (include/fem.h, fem_batch_*)."""
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        arr = (_VP * len(self.ops))(*[o._h for o in self.ops])
+        h = _VP()
+        _check(lib().fem_batch_create(arr, len(self.ops), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fem_batch_destroy(self._h)
+            self._h = None
+
+    def _vecs(self, bs, xs):
+        assert len(bs) == len(self.ops) == len(xs)
+        return (_VP * len(bs))(*[_ptr(b) for b in bs]), (_VP * len(xs))(*[_ptr(x) for x in xs])
+
+    def solve(self, bs, xs, rtol=1e-10, inner_rtol=1e-5, maxit=100000, max_outer=20):
+        o = _CgOpts(PC_JACOBI, int(maxit), float(rtol), 0, float(inner_rtol), int(max_outer))
+        st = (_CgStats * len(self.ops))()
+        bv, xv = self._vecs(bs, xs)
+        rc = lib().fem_batch_solve(self._h, bv, xv, ctypes.byref(o), st)
+        if rc not in (0, 5):
+            _check(rc)
+        return [_stats(s) for s in st]
+
+    def set_shape(self, nt_choice, blocks_per_sm=0, timeout_ms=2000.0):
+        _check(lib().fem_batch_set_shape(self._h, nt_choice, blocks_per_sm, timeout_ms))
+
+    def autotune(self, bs, xs, iters=10):
+        r = _TuneResult()
+        bv, xv = self._vecs(bs, xs)
+        _check(lib().fem_batch_autotune(self._h, bv, xv, iters, ctypes.byref(r)))
+        return dict(nt_choice=r.epb_choice, blocks_per_sm=r.blocks_per_sm, us_per_iter=r.us,
+                    candidates=r.candidates)
+
+    def barrier_selftest(self, timeout_ms=300.0):
+        """Status code returned when the persistent kernel's barrier is made
+        to wait for an arrival that never comes (FEM_ETIMEOUT expected)."""
+        return lib().fem_batch_barrier_selftest(self._h, timeout_ms)

@@ -1,0 +1,96 @@
+// Launch and dispatch of the fused apply over (P, q, kind) and the launch
+// shape: EPB (elements per block) and blocks per SM, the two parameters the
+// autotuner picks.  Included once per arithmetic type (apply_f64.cu,
+// apply_f32.cu).
+#pragma once
+#include "apply_kernel.cuh"
+
+namespace fem_apply {
+
+// Elements-per-block candidates: index 0 = default (about 256 threads),
+// 1 = half of it, 2 = twice it.  Only shapes with <= 1024 threads and
+// <= 200 KB of shared memory are valid.
+template <int Q, int CHOICE>
+struct EpbChoice {
+  static constexpr int D = DefaultEpb<Q>::value;
+  static constexpr int value = CHOICE == 0 ? D : (CHOICE == 1 ? (D / 2 > 0 ? D / 2 : 1) : 2 * D);
+};
+
+template <typename T, int P, int Q, int KIND, bool COLLOC, int EPB>
+int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
+  constexpr int NT = ApplyShape<Q, EPB>::NT;
+  constexpr size_t smem = apply_smem_bytes<T, Q, P, KIND, EPB>();
+  if constexpr (NT > 1024 || smem > 200 * 1024) {
+    fem_set_error("apply: launch shape EPB=%d not valid for P=%d q=%d", EPB, P, Q);
+    return FEM_EINVAL;
+  } else {
+    auto kern = fem_apply_kernel<T, P, Q, KIND, COLLOC, EPB>;
+    static int max_bps = -1;
+    if (max_bps < 0) {
+      FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+      max_bps = per_sm < 1 ? 1 : per_sm;
+    }
+    const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
+    const int64_t ngroups = (prm.nsel + EPB - 1) / EPB;
+    int64_t grid = (int64_t)op->nsm * use;
+    if (grid > ngroups) grid = ngroups;
+    if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, NT, smem, op->stream()>>>(prm);
+    FEM_CHECK_LAUNCH();
+    return FEM_OK;
+  }
+}
+
+template <typename T, int P, int Q, int KIND, bool COLLOC>
+int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
+  switch (choice) {
+    case 1: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 1>::value>(op, prm, bps);
+    case 2: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);
+    default: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 0>::value>(op, prm, bps);
+  }
+}
+
+// Diffusion shapes are tunable; mass and the q = p+1 Gauss variant use the default.
+template <typename T, int P>
+int dispatch_q(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
+  constexpr int QG = (P + 1 <= FEM_MAX_Q) ? P + 1 : P;
+  const bool diff = op->kind == FEM_DIFFUSION;
+  if (op->Q == P) {
+    if (op->colloc)
+      return diff ? launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps)
+                  : launch_shape<T, P, P, FEM_MASS, true, EpbChoice<P, 0>::value>(op, prm, bps);
+    return diff ? launch_shape<T, P, P, FEM_DIFFUSION, false, EpbChoice<P, 0>::value>(op, prm, bps)
+                : launch_shape<T, P, P, FEM_MASS, false, EpbChoice<P, 0>::value>(op, prm, bps);
+  }
+  if (op->Q == P + 1 && QG == P + 1)
+    return diff ? launch_epb<T, P, QG, FEM_DIFFUSION, false>(op, prm, choice, bps)
+                : launch_shape<T, P, QG, FEM_MASS, false, EpbChoice<QG, 0>::value>(op, prm, bps);
+  fem_set_error("apply: unsupported (P, q) = (%d, %d)", P, op->Q);
+  return FEM_EINVAL;
+}
+
+template <typename T>
+int dispatch(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
+  switch (op->P) {
+    case 2: return dispatch_q<T, 2>(op, prm, choice, bps);
+    case 3: return dispatch_q<T, 3>(op, prm, choice, bps);
+    case 4: return dispatch_q<T, 4>(op, prm, choice, bps);
+    case 5: return dispatch_q<T, 5>(op, prm, choice, bps);
+    case 6: return dispatch_q<T, 6>(op, prm, choice, bps);
+    case 7: return dispatch_q<T, 7>(op, prm, choice, bps);
+    case 8: return dispatch_q<T, 8>(op, prm, choice, bps);
+    case 9: return dispatch_q<T, 9>(op, prm, choice, bps);
+  }
+  fem_set_error("apply: unsupported P = %d", op->P);
+  return FEM_EINVAL;
+}
+
+// Number of valid EPB choices for this operator (1 if not tunable).
+inline int epb_choices(const fem_op *op) {
+  return op->kind == FEM_DIFFUSION && (op->colloc || op->Q == op->P + 1) ? 3 : 1;
+}
+
+}  // namespace fem_apply

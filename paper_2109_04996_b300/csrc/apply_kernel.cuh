@@ -1,7 +1,9 @@
-// Fused operator apply  y = G^T B^T D B G x  (section "libCEED": the
-// operator decomposition; the fused single-kernel form of section "Nek and
-// MFEM" / "libCEED" CPU and GPU performance).  One kernel per call:
+// Templates of the fused operator apply  y = G^T B^T D B G x  (section
+// "libCEED": operator decomposition; fused single-kernel operator).  Shared by
+// the single-operator kernels (apply_f64.cu, apply_f32.cu) and the batched
+// persistent solver (batch.cu).
 //
+// Per element:
 //   G    gather of the element's (p+1)^3 values through elem_nodes,
 //   B    sum-factorized interpolation to the q^3 quadrature points, one
 //        direction at a time (section "Benchmarks", tensor-product sum
@@ -14,12 +16,13 @@
 // Thread layout: q x q threads per element ("slab"); thread (i, j) owns the
 // column of quadrature points (i, j, 0..q-1) in registers, contractions along
 // the third direction stay in registers, the other two go through a q^3 cube
-// in shared memory.  Several elements share a block; blocks loop over element
-// groups (grid-stride) so that the grid is a small multiple of the SM count.
-// Gauss-Lobatto with q = p+1 (BP5/BP6) skips the interpolation (identity).
+// in shared memory.  EPB elements share a block (the autotuned shape); blocks
+// loop over element groups.  Gauss-Lobatto with q = p+1 (BP5/BP6) skips the
+// interpolation (identity).
+#pragma once
 #include "fem_internal.h"
 
-namespace {
+namespace fem_apply {
 
 template <typename T>
 struct ApplyParams {
@@ -36,54 +39,85 @@ struct ApplyParams {
   double *partials;           // fused x.y (optional)
   unsigned *counter;
   double *dot_out;
+  int x_l2_only = 0;          // 1: gather x with L2-only loads (x written by
+                              // other blocks of a persistent kernel)
 };
 
+template <typename T>
+__device__ __forceinline__ T gather_load(const T *p, int l2_only) {
+  return l2_only ? __ldcg(p) : *p;
+}
+
+// Elements per block of the default shape: about 256 threads.
 template <int Q>
+struct DefaultEpb {
+  static constexpr int value = (256 / (Q * Q)) > 0 ? (256 / (Q * Q)) : 1;
+};
+
+template <int Q, int EPB>
 struct ApplyShape {
   static constexpr int Q2 = Q * Q;
-  // elements per block: about 256 threads
-  static constexpr int EPB = (256 / Q2) > 0 ? (256 / Q2) : 1;
   // block size rounded up to whole warps; the extra threads ("padding") share
   // the last slot's shared memory for reads but never write it
   static constexpr int NT = ((Q2 * EPB + 31) / 32) * 32;
 };
 
+template <typename T, int Q, int P, int KIND, int EPB>
+constexpr size_t apply_smem_bytes() {
+  return sizeof(T) * (Q * P + Q * Q + (size_t)EPB * ((KIND == FEM_DIFFUSION) ? 3 : 2) * Q * Q * Q);
+}
+
 template <typename T>
 __device__ __forceinline__ void atomic_add(T *a, T v) { atomicAdd(a, v); }
 
-template <typename T, int P, int Q, int KIND, bool COLLOC>
-__global__ void __launch_bounds__(ApplyShape<Q>::NT)
-    fem_apply_kernel(const ApplyParams<T> prm) {
-  using S = ApplyShape<Q>;
+// Thread-local view of one block: slot, slab coordinates and shared buffers.
+template <typename T, int P, int Q, int KIND, int EPB>
+struct Slab {
+  int slot_raw, slot, tx, ty;
+  bool live;
+  T *sB, *sD, *su, *sv, *sw;
+  __device__ Slab(unsigned char *smem_raw) {
+    constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
+    constexpr int NCUBE = (KIND == FEM_DIFFUSION) ? 3 : 2;
+    sB = reinterpret_cast<T *>(smem_raw);
+    sD = sB + Q * P;
+    T *cube = sD + Q * Q;
+    slot_raw = threadIdx.x / Q2;
+    live = slot_raw < EPB;
+    slot = live ? slot_raw : EPB - 1;
+    const int t = threadIdx.x - slot_raw * Q2;
+    tx = t % Q; ty = t / Q;
+    su = cube + slot * NCUBE * Q3;
+    sv = su + Q3;
+    sw = (NCUBE == 3) ? sv + Q3 : sv;
+  }
+  __device__ void load_tables(const T *B, const T *Dq) {
+    for (int i = threadIdx.x; i < Q * P; i += blockDim.x) sB[i] = B[i];
+    for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) sD[i] = Dq[i];
+  }
+};
+
+// One group of EPB elements (elements g*EPB .. g*EPB + EPB - 1 of the
+// selection), all components.  Every thread of the block calls it (it
+// synchronizes the block).  Adds this thread's share of x.y to `dot`.
+template <typename T, int P, int Q, int KIND, bool COLLOC, int EPB>
+__device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g,
+                                            const Slab<T, P, Q, KIND, EPB> &sl, double &dot) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P2 = P * P, P3 = P * P * P;
   constexpr int ND = (KIND == FEM_DIFFUSION) ? 6 : 1;
-  constexpr int NCUBE = (KIND == FEM_DIFFUSION) ? 3 : 2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sB = reinterpret_cast<T *>(smem_raw);  // [Q][P]
-  T *sD = sB + Q * P;                       // [Q][Q]
-  T *cube = sD + Q * Q;
-  const int slot_raw = threadIdx.x / Q2;
-  const bool live = slot_raw < S::EPB;  // false for padding threads
-  const int slot = live ? slot_raw : S::EPB - 1;
-  const int t = threadIdx.x - slot_raw * Q2;
-  const int tx = t % Q, ty = t / Q;
-  T *su = cube + slot * NCUBE * Q3;
-  T *sv = su + Q3;
-  T *sw = (NCUBE == 3) ? sv + Q3 : sv;
-  for (int i = threadIdx.x; i < Q * P; i += blockDim.x) sB[i] = prm.B[i];
-  for (int i = threadIdx.x; i < Q * Q; i += blockDim.x) sD[i] = prm.Dq[i];
-  __syncthreads();
-
-  double dot = 0.0;
+  const int tx = sl.tx, ty = sl.ty;
+  const bool live = sl.live;
+  const T *sB = sl.sB;
+  const T *sD = sl.sD;
+  T *su = sl.su, *sv = sl.sv, *sw = sl.sw;
+  (void)sw;
   const int64_t N = prm.N;
-  const int64_t ngroups = (prm.nsel + S::EPB - 1) / S::EPB;
-  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    const int64_t k_el = g * S::EPB + slot_raw;
-    const bool valid = live && (k_el < prm.nsel);
-    int64_t e = 0;
-    if (valid) e = prm.list ? (int64_t)prm.list[k_el] : k_el;
-    const int32_t *en = prm.elem_nodes + e * P3;
-    const T *qd = prm.qdata + e * (int64_t)(ND * Q3) + (ty * Q + tx);
+  const int64_t k_el = g * EPB + sl.slot_raw;
+  const bool valid = live && (k_el < prm.nsel);
+  int64_t e = 0;
+  if (valid) e = prm.list ? (int64_t)prm.list[k_el] : k_el;
+  const int32_t *en = prm.elem_nodes + e * P3;
+  const T *qd = prm.qdata + e * (int64_t)(ND * Q3) + (ty * Q + tx);
     for (int c = 0; c < prm.ncomp; c++) {
       const T *xc = prm.x + c * N;
       T *yc = prm.y + c * N;
@@ -93,7 +127,7 @@ __global__ void __launch_bounds__(ApplyShape<Q>::NT)
 #pragma unroll
           for (int k = 0; k < Q; k++) {
             const int64_t gi = en[tx + P * ty + P2 * k];
-            const T xv = xc[gi];
+            const T xv = gather_load(&xc[gi], prm.x_l2_only);
             const T v = qd[k * Q2] * xv;
             atomic_add(&yc[gi], v);
             dot += (double)v * (double)xv;
@@ -103,7 +137,7 @@ __global__ void __launch_bounds__(ApplyShape<Q>::NT)
         // ---- BP5/BP6: gradients directly on the Gauss-Lobatto nodes
         T u[Q];
 #pragma unroll
-        for (int k = 0; k < Q; k++) u[k] = valid ? xc[en[tx + P * ty + P2 * k]] : T(0);
+        for (int k = 0; k < Q; k++) u[k] = valid ? gather_load(&xc[en[tx + P * ty + P2 * k]], prm.x_l2_only) : T(0);
         if (live) {
 #pragma unroll
           for (int k = 0; k < Q; k++) su[(k * Q + ty) * Q + tx] = u[k];
@@ -159,7 +193,7 @@ __global__ void __launch_bounds__(ApplyShape<Q>::NT)
         const bool own = (tx < P) && (ty < P);
         T r[P];
 #pragma unroll
-        for (int k = 0; k < P; k++) r[k] = (valid && own) ? xc[en[tx + P * ty + P2 * k]] : T(0);
+        for (int k = 0; k < P; k++) r[k] = (valid && own) ? gather_load(&xc[en[tx + P * ty + P2 * k]], prm.x_l2_only) : T(0);
         T tq[Q];
         // B along z (registers)
 #pragma unroll
@@ -289,7 +323,19 @@ __global__ void __launch_bounds__(ApplyShape<Q>::NT)
         }
       }
     }
-  }
+}
+
+template <typename T, int P, int Q, int KIND, bool COLLOC, int EPB>
+__global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
+    fem_apply_kernel(const ApplyParams<T> prm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Slab<T, P, Q, KIND, EPB> sl(smem_raw);
+  sl.load_tables(prm.B, prm.Dq);
+  __syncthreads();
+  double dot = 0.0;
+  const int64_t ngroups = (prm.nsel + EPB - 1) / EPB;
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
+    apply_group<T, P, Q, KIND, COLLOC, EPB>(prm, g, sl, dot);
   if (prm.dot_out) {
     double v[1] = {dot};
     __shared__ double tot[1];
@@ -298,94 +344,4 @@ __global__ void __launch_bounds__(ApplyShape<Q>::NT)
   }
 }
 
-template <typename T, int P, int Q, int KIND, bool COLLOC>
-int launch_one(fem_op *op, const ApplyParams<T> &prm) {
-  using S = ApplyShape<Q>;
-  constexpr int NCUBE = (KIND == FEM_DIFFUSION) ? 3 : 2;
-  const size_t smem = sizeof(T) * (Q * P + Q * Q + (size_t)S::EPB * NCUBE * Q * Q * Q);
-  auto kern = fem_apply_kernel<T, P, Q, KIND, COLLOC>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
-  int dev = 0, nsm = 0, per_sm = 0;
-  FEM_CUDA_TRY(cudaGetDevice(&dev));
-  FEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, smem));
-  if (per_sm < 1) per_sm = 1;
-  const int64_t ngroups = (prm.nsel + S::EPB - 1) / S::EPB;
-  int64_t grid = (int64_t)nsm * per_sm;
-  if (grid > ngroups) grid = ngroups;
-  if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
-  if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, S::NT, smem, op->stream()>>>(prm);
-  FEM_CHECK_LAUNCH();
-  return FEM_OK;
-}
-
-template <typename T, int P>
-int dispatch_q(fem_op *op, const ApplyParams<T> &prm) {
-  constexpr int QG = (P + 1 <= FEM_MAX_Q) ? P + 1 : P;
-  const bool diff = op->kind == FEM_DIFFUSION;
-  if (op->Q == P) {
-    if (op->colloc)
-      return diff ? launch_one<T, P, P, FEM_DIFFUSION, true>(op, prm)
-                  : launch_one<T, P, P, FEM_MASS, true>(op, prm);
-    return diff ? launch_one<T, P, P, FEM_DIFFUSION, false>(op, prm)
-                : launch_one<T, P, P, FEM_MASS, false>(op, prm);
-  }
-  if (op->Q == P + 1 && QG == P + 1)
-    return diff ? launch_one<T, P, QG, FEM_DIFFUSION, false>(op, prm)
-                : launch_one<T, P, QG, FEM_MASS, false>(op, prm);
-  fem_set_error("apply: unsupported (P, q) = (%d, %d)", P, op->Q);
-  return FEM_EINVAL;
-}
-
-template <typename T>
-int dispatch(fem_op *op, const ApplyParams<T> &prm) {
-  switch (op->P) {
-    case 2: return dispatch_q<T, 2>(op, prm);
-    case 3: return dispatch_q<T, 3>(op, prm);
-    case 4: return dispatch_q<T, 4>(op, prm);
-    case 5: return dispatch_q<T, 5>(op, prm);
-    case 6: return dispatch_q<T, 6>(op, prm);
-    case 7: return dispatch_q<T, 7>(op, prm);
-    case 8: return dispatch_q<T, 8>(op, prm);
-    case 9: return dispatch_q<T, 9>(op, prm);
-  }
-  fem_set_error("apply: unsupported P = %d", op->P);
-  return FEM_EINVAL;
-}
-
-}  // namespace
-
-int fem_launch_apply_f64(fem_op *op, const double *x, double *y,
-                         const int32_t *list, int64_t nsel, double *dot_out) {
-  ApplyParams<double> prm;
-  prm.x = x; prm.y = y;
-  prm.elem_nodes = op->mesh->d_elem_nodes;
-  prm.list = list; prm.nsel = nsel;
-  prm.N = op->N; prm.ncomp = op->ncomp;
-  prm.qdata = op->d_qdata; prm.B = op->d_B; prm.Dq = op->d_Dq;
-  prm.partials = op->d_partials; prm.counter = op->d_counter; prm.dot_out = dot_out;
-  if (nsel == 0) return FEM_OK;
-  return dispatch<double>(op, prm);
-}
-
-int fem_launch_apply_f32(fem_op *op, const float *x, float *y,
-                         const int32_t *list, int64_t nsel, double *dot_out) {
-  if (!op->d_qdata32) {
-    fem_set_error("apply_f32: operator was not created with FEM_F32");
-    return FEM_EINVAL;
-  }
-  ApplyParams<float> prm;
-  prm.x = x; prm.y = y;
-  prm.elem_nodes = op->mesh->d_elem_nodes;
-  prm.list = list; prm.nsel = nsel;
-  prm.N = op->N; prm.ncomp = op->ncomp;
-  prm.qdata = op->d_qdata32; prm.B = op->d_B32; prm.Dq = op->d_Dq32;
-  prm.partials = op->d_partials; prm.counter = op->d_counter; prm.dot_out = dot_out;
-  if (nsel == 0) return FEM_OK;
-  return dispatch<float>(op, prm);
-}
+}  // namespace fem_apply

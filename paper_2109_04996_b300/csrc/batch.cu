@@ -1,0 +1,740 @@
+// Batched solve: many independent BP3-type problems (scalar or vector
+// diffusion, Gauss-Legendre q = p+2, any order 1..8, any size) solved
+// together.  Each problem runs the mixed-precision method of refine.cu (FP64
+// iterative refinement around an FP32 inner Jacobi-PCG with FP64 dot products
+// and scalars); the inner iterations of ALL problems run in one persistent
+// cooperative kernel per outer step.  The paper batches small dense products
+// across elements (section "Ecosystem", batched BLAS); here whole solves are
+// batched so that small problems share the GPU instead of each paying launch
+// and reduction latency.
+//
+// Persistent kernel, global iteration k (all active problems advance
+// together; a problem leaves when its inner test is met):
+//   apply phase     work items (problem, element group): y = A_32 p and the
+//                   problem's p^T A p, accumulated into pAp[k&1];
+//   barrier
+//   update phase    work items (problem, vector chunk): alpha, d, r, z and
+//                   r^T z, ||r||^2 into rz[k&1], rr[k&1];
+//   barrier
+//   direction phase beta = rz[k&1] / rz[(k+1)&1]; p = z + beta p; y = 0; block 0
+//                   decides each problem's inner convergence;
+//   barrier
+// The ping-pong slots are cleared one phase after their last reader (see the
+// comments at each clear).  Grid barriers are counter/generation barriers on
+// global memory with a wall-clock limit: on expiry the kernel records
+// FEM_ETIMEOUT and every block returns.
+#include <limits.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "apply_kernel.cuh"
+
+using fem_apply::ApplyParams;
+using fem_apply::Slab;
+using fem_apply::apply_group;
+using fem_apply::apply_smem_bytes;
+
+struct BatchProblem {
+  int P, Q, ncomp;
+  int64_t N, E, n;
+  const int32_t *elem_nodes;
+  const uint8_t *dir;
+  const float *qdata32, *B32, *Dq32;
+  const double *qdata64, *B64, *Dq64;
+  const double *diag;
+  // outer (FP64) and inner (FP32) vectors
+  const double *b;
+  double *x, *y64;
+  float *r, *z, *p, *y, *d, *dinv;
+};
+
+struct BatchScalars {
+  double pAp[2], rz[2], rr[2];
+  double rr64, bb64, rz0, rr0;   // residual-kernel accumulators
+  double thresh;                  // inner threshold on ||r||^2
+  double rr64_last, bb64_last;    // outer residual of the latest check
+  int done_at;                    // iteration at which the inner solve ended
+  int iter;                       // inner iterations of this outer step
+  int total_iter, outer, converged, status;
+};
+
+struct BatchSync {
+  unsigned count, gen;
+  int error;
+  int pad;
+};
+
+struct fem_batch {
+  int n = 0;
+  std::vector<fem_op *> ops;
+  cudaStream_t stream = nullptr;
+  BatchProblem *d_prob = nullptr;
+  BatchScalars *d_sc = nullptr;
+  BatchSync *d_sync = nullptr;
+  int64_t *d_gstart = nullptr;   // apply items prefix (inner shape)
+  int64_t *d_gstart64 = nullptr; // apply items prefix (FP64 shape)
+  int64_t *d_cstart = nullptr;   // vector chunk prefix
+  int64_t n_items = 0, n_items64 = 0, n_chunks = 0;
+  std::vector<BatchProblem> h_prob;
+  std::vector<void *> allocs;
+  int nt_choice = 1;             // inner kernel block size index: 128, 256, 512
+  int bps = 0;                   // blocks per SM of the persistent kernel (0 = max)
+  double timeout_ms = 2000.0;
+  int64_t bytes = 0;
+};
+
+namespace {
+
+constexpr int kChunk = 2048;     // vector entries per work item
+constexpr int kNT64 = 256;       // block size of the FP64 batched apply
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier with a wall-clock limit.  Returns false (every block) once
+// any block has recorded an error.  extra: arrivals that never come (a test
+// hook that makes the wait run out); 0 in normal use.
+__device__ bool grid_barrier(BatchSync *s, unsigned extra, unsigned long long timeout_ns) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = &s->gen;
+    volatile int *verr = &s->error;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&s->count, 1u);
+    if (arrived == gridDim.x + extra - 1) {
+      atomicExch(&s->count, 0u);
+      __threadfence();
+      atomicAdd(&s->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == g) {
+        if (*verr) break;
+        if (global_ns() - t0 > timeout_ns) {
+          atomicCAS(&s->error, 0, (int)FEM_ETIMEOUT);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    s_ok = (*verr == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = fem_warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; w++) s += red[w];
+  return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ int find_problem(const int64_t *start, int n, int64_t item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int NT, int Q>
+struct BatchEpb {
+  static constexpr int value = NT / (Q * Q) > 0 ? NT / (Q * Q) : 1;
+};
+
+// One element group of problem `pr` in precision T (FP32 inner / FP64 outer).
+template <typename T, int NT, int P>
+__device__ void batch_group(const BatchProblem &pr, int64_t g, const T *x, T *y,
+                            unsigned char *smem, double &dot) {
+  constexpr int Q = P + 1;
+  constexpr int EPB = BatchEpb<NT, Q>::value;
+  ApplyParams<T> prm;
+  prm.x = x; prm.y = y; prm.elem_nodes = pr.elem_nodes; prm.list = nullptr; prm.nsel = pr.E;
+  prm.N = pr.N; prm.ncomp = pr.ncomp;
+  if constexpr (sizeof(T) == 4) { prm.qdata = (const T *)pr.qdata32; prm.B = (const T *)pr.B32; prm.Dq = (const T *)pr.Dq32; }
+  else { prm.qdata = (const T *)pr.qdata64; prm.B = (const T *)pr.B64; prm.Dq = (const T *)pr.Dq64; }
+  prm.partials = nullptr; prm.counter = nullptr; prm.dot_out = nullptr;
+  prm.x_l2_only = 1;  // x (the direction p) was written by other blocks
+  Slab<T, P, Q, FEM_DIFFUSION, EPB> sl(smem);
+  __syncthreads();  // previous item may still read the tables
+  sl.load_tables(prm.B, prm.Dq);
+  __syncthreads();
+  apply_group<T, P, Q, FEM_DIFFUSION, false, EPB>(prm, g, sl, dot);
+}
+
+template <typename T, int NT>
+__device__ void batch_group_p(const BatchProblem &pr, int64_t g, const T *x, T *y,
+                              unsigned char *smem, double &dot) {
+  switch (pr.P) {
+    case 2: batch_group<T, NT, 2>(pr, g, x, y, smem, dot); break;
+    case 3: batch_group<T, NT, 3>(pr, g, x, y, smem, dot); break;
+    case 4: batch_group<T, NT, 4>(pr, g, x, y, smem, dot); break;
+    case 5: batch_group<T, NT, 5>(pr, g, x, y, smem, dot); break;
+    case 6: batch_group<T, NT, 6>(pr, g, x, y, smem, dot); break;
+    case 7: batch_group<T, NT, 7>(pr, g, x, y, smem, dot); break;
+    case 8: batch_group<T, NT, 8>(pr, g, x, y, smem, dot); break;
+    case 9: batch_group<T, NT, 9>(pr, g, x, y, smem, dot); break;
+  }
+}
+
+template <typename T, int NT>
+constexpr size_t batch_smem() {
+  size_t m = 0;
+#define FEM_BS(P) { size_t s = apply_smem_bytes<T, P + 1, P, FEM_DIFFUSION, BatchEpb<NT, P + 1>::value>(); if (s > m) m = s; }
+  FEM_BS(2) FEM_BS(3) FEM_BS(4) FEM_BS(5) FEM_BS(6) FEM_BS(7) FEM_BS(8) FEM_BS(9)
+#undef FEM_BS
+  return m;
+}
+
+struct BatchArgs {
+  BatchProblem *prob;
+  BatchScalars *sc;
+  BatchSync *sync;
+  const int64_t *gstart;   // [n+1] apply items
+  const int64_t *cstart;   // [n+1] vector chunks
+  int n;
+  int maxit;
+  unsigned barrier_extra;
+  unsigned long long timeout_ns;
+};
+
+// ---- the persistent inner FP32 PCG over all problems
+template <int NT>
+__global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32];
+  const int64_t n_items = a.gstart[a.n], n_chunks = a.cstart[a.n];
+  for (int k = 0; k < a.maxit; k++) {
+    const int cur = k & 1, prev = cur ^ 1;
+    // -------- apply phase
+    if (blockIdx.x == 0) {
+      // rz[cur], rr[cur] were last read in the direction phase of k-1
+      for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        a.sc[i].rz[cur] = 0.0;
+        a.sc[i].rr[cur] = 0.0;
+      }
+    }
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+      const int i = find_problem(a.gstart, a.n, it);
+      if (__ldcg(&a.sc[i].done_at) < k) continue;   // uniform per block
+      const BatchProblem &pr = a.prob[i];
+      double dot = 0.0;
+      batch_group_p<float, NT>(pr, it - a.gstart[i], pr.p, pr.y, smem, dot);
+      const double s = block_sum(dot, red);
+      if (threadIdx.x == 0) atomicAdd(&a.sc[i].pAp[cur], s);
+    }
+    if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
+    // -------- update phase
+    for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
+      const int i = find_problem(a.cstart, a.n, it);
+      if (__ldcg(&a.sc[i].done_at) < k) continue;
+      const BatchProblem &pr = a.prob[i];
+      const double pAp = __ldcg(&a.sc[i].pAp[cur]);
+      const double alpha = __ldcg(&a.sc[i].rz[prev]) / pAp;
+      if (!(pAp > 0.0) || !isfinite(alpha)) continue;
+      const float af = (float)alpha;
+      const int64_t lo = (it - a.cstart[i]) * kChunk;
+      const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
+      double v0 = 0.0, v1 = 0.0;
+      for (int64_t j = lo + threadIdx.x; j < hi; j += NT) {
+        const bool fixed = pr.dir && pr.dir[j % pr.N];
+        float r = pr.r[j];
+        pr.d[j] += af * pr.p[j];
+        if (!fixed) r -= af * __ldcg(&pr.y[j]);  // y: atomics of other blocks
+        pr.r[j] = r;
+        const float z = pr.dinv[j] * r;
+        pr.z[j] = z;
+        v0 += (double)r * (double)z;
+        v1 += (double)r * (double)r;
+      }
+      const double s0 = block_sum(v0, red);
+      const double s1 = block_sum(v1, red);
+      if (threadIdx.x == 0) {
+        atomicAdd(&a.sc[i].rz[cur], s0);
+        atomicAdd(&a.sc[i].rr[cur], s1);
+      }
+    }
+    if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
+    // -------- direction phase
+    if (blockIdx.x == 0) for (int ii = threadIdx.x; ii < a.n; ii += blockDim.x) {
+      BatchScalars &s = a.sc[ii];
+      if (!(s.done_at < k)) {
+        // pAp[prev] was last read in the update phase of k-1
+        s.pAp[prev] = 0.0;
+        const double pAp = __ldcg(&s.pAp[cur]);
+        const bool ok = (pAp > 0.0) && isfinite(__ldcg(&s.rz[prev]) / pAp);
+        if (ok) { s.iter += 1; s.total_iter += 1; }
+        const double rzc = __ldcg(&s.rz[cur]), rrc = __ldcg(&s.rr[cur]);
+        if (!ok || !isfinite(rzc) || rrc <= s.thresh || s.iter >= a.maxit)
+          s.done_at = k;
+      }
+    }
+    for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
+      const int i = find_problem(a.cstart, a.n, it);
+      if (__ldcg(&a.sc[i].done_at) < k) continue;
+      const BatchProblem &pr = a.prob[i];
+      const float beta = (float)(__ldcg(&a.sc[i].rz[cur]) / __ldcg(&a.sc[i].rz[prev]));
+      const int64_t lo = (it - a.cstart[i]) * kChunk;
+      const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
+      for (int64_t j = lo + threadIdx.x; j < hi; j += NT) {
+        pr.p[j] = pr.z[j] + beta * pr.p[j];
+        pr.y[j] = 0.0f;
+      }
+    }
+    if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
+    bool all = true;
+    for (int i = 0; i < a.n; i++) all = all && (__ldcg(&a.sc[i].done_at) <= k);
+    if (all) return;
+  }
+}
+
+// ---- FP64 batched apply y64 = A_64 x for every problem not yet converged
+__global__ void __launch_bounds__(kNT64) batch_apply64_kernel(const BatchArgs a, const int64_t *gstart64) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t n_items = gstart64[a.n];
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int i = find_problem(gstart64, a.n, it);
+    if (a.sc[i].converged) continue;
+    const BatchProblem &pr = a.prob[i];
+    double dot = 0.0;
+    batch_group_p<double, kNT64>(pr, it - gstart64[i], pr.x, pr.y64, smem, dot);
+  }
+}
+
+// r64 = M (b - A x); inner start d = 0, r = r64, z = dinv r, p = z
+__global__ void batch_residual_kernel(const BatchArgs a) {
+  __shared__ double red[32];
+  const int64_t n_chunks = a.cstart[a.n];
+  for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
+    const int i = find_problem(a.cstart, a.n, it);
+    if (a.sc[i].converged) continue;
+    const BatchProblem &pr = a.prob[i];
+    const int64_t lo = (it - a.cstart[i]) * kChunk;
+    const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
+    double v[4] = {0, 0, 0, 0};
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+      const bool fixed = pr.dir && pr.dir[j % pr.N];
+      const double bj = fixed ? 0.0 : pr.b[j];
+      const double r64 = fixed ? 0.0 : bj - pr.y64[j];
+      const float r = (float)r64, z = pr.dinv[j] * r;
+      pr.r[j] = r; pr.z[j] = z; pr.p[j] = z; pr.d[j] = 0.0f; pr.y[j] = 0.0f;
+      pr.y64[j] = 0.0;
+      v[0] += r64 * r64; v[1] += bj * bj; v[2] += (double)r * z; v[3] += (double)r * r;
+    }
+    for (int q = 0; q < 4; q++) {
+      const double s = block_sum(v[q], red);
+      if (threadIdx.x == 0) {
+        double *dst = q == 0 ? &a.sc[i].rr64 : q == 1 ? &a.sc[i].bb64 : q == 2 ? &a.sc[i].rz0 : &a.sc[i].rr0;
+        atomicAdd(dst, s);
+      }
+    }
+  }
+}
+
+// Outer test and inner start state, one thread per problem.
+__global__ void batch_finalize_kernel(const BatchArgs a, double rtol2, double inner_rtol2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  BatchScalars &s = a.sc[i];
+  if (!s.converged) {
+    s.rr64_last = s.rr64; s.bb64_last = s.bb64;
+    if (!isfinite(s.rr64) || !isfinite(s.rz0)) { s.status = FEM_EBREAKDOWN; s.converged = 1; }
+    else if (!(s.bb64 > 0.0) || s.rr64 <= rtol2 * s.bb64) s.converged = 1;
+  }
+  s.pAp[0] = s.pAp[1] = 0.0;
+  s.rz[0] = 0.0; s.rz[1] = s.rz0;   // iteration 0 reads rz[1]
+  s.rr[0] = s.rr[1] = 0.0;
+  s.thresh = inner_rtol2 * s.rr0;
+  s.iter = 0;
+  s.done_at = s.converged ? -1 : INT_MAX;
+}
+
+// x += d for problems still refining; clear the residual accumulators.
+__global__ void batch_correct_kernel(const BatchArgs a) {
+  const int64_t n_chunks = a.cstart[a.n];
+  for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
+    const int i = find_problem(a.cstart, a.n, it);
+    if (a.sc[i].converged) continue;
+    const BatchProblem &pr = a.prob[i];
+    const int64_t lo = (it - a.cstart[i]) * kChunk;
+    const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) pr.x[j] += (double)pr.d[j];
+  }
+}
+
+__global__ void batch_step_end_kernel(const BatchArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  BatchScalars &s = a.sc[i];
+  if (!s.converged) s.outer += 1;
+  s.rr64 = s.bb64 = s.rz0 = s.rr0 = 0.0;
+}
+
+__global__ void batch_prepare_kernel(const BatchArgs a) {
+  const int64_t n_chunks = a.cstart[a.n];
+  for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
+    const int i = find_problem(a.cstart, a.n, it);
+    const BatchProblem &pr = a.prob[i];
+    const int64_t lo = (it - a.cstart[i]) * kChunk;
+    const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+      const int64_t node = j % pr.N;
+      if (pr.dir && pr.dir[node]) pr.x[j] = 0.0;
+      pr.y64[j] = 0.0;
+      pr.dinv[j] = (pr.dir && pr.dir[node]) ? 0.0f : (float)(1.0 / pr.diag[node]);
+    }
+  }
+}
+
+const int kNtChoices[3] = {128, 256, 512};
+
+template <int NT>
+int launch_inner_nt(fem_batch *b, const BatchArgs &a, int bps) {
+  auto kern = batch_inner_kernel<NT>;
+  constexpr size_t smem = batch_smem<float, NT>();
+  FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  if (per_sm < 1) { fem_set_error("batch: inner kernel does not fit on an SM"); return FEM_ECUDA; }
+  const int use = (bps <= 0 || bps > per_sm) ? per_sm : bps;
+  int nsm = b->ops[0]->nsm;
+  dim3 grid((unsigned)(nsm * use)), block(NT);
+  void *args[] = {(void *)&a};
+  FEM_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, grid, block, args, smem, b->stream));
+  return FEM_OK;
+}
+
+int launch_inner(fem_batch *b, const BatchArgs &a, int nt_choice, int bps) {
+  switch (nt_choice) {
+    case 0: return launch_inner_nt<128>(b, a, bps);
+    case 2: return launch_inner_nt<512>(b, a, bps);
+    default: return launch_inner_nt<256>(b, a, bps);
+  }
+}
+
+int64_t groups_for(const BatchProblem &p, int nt) {
+  const int Q = p.Q;
+  int epb = nt / (Q * Q);
+  if (epb < 1) epb = 1;
+  return (p.E + epb - 1) / epb;
+}
+
+int build_items(fem_batch *b, int nt) {
+  std::vector<int64_t> gs(b->n + 1, 0);
+  for (int i = 0; i < b->n; i++) gs[i + 1] = gs[i] + groups_for(b->h_prob[i], nt);
+  b->n_items = gs[b->n];
+  FEM_CUDA_TRY(cudaMemcpyAsync(b->d_gstart, gs.data(), sizeof(int64_t) * (b->n + 1),
+                               cudaMemcpyHostToDevice, b->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return FEM_OK;
+}
+
+BatchArgs args_of(fem_batch *b, int maxit, unsigned extra) {
+  BatchArgs a;
+  a.prob = b->d_prob; a.sc = b->d_sc; a.sync = b->d_sync; a.gstart = b->d_gstart;
+  a.cstart = b->d_cstart; a.n = b->n; a.maxit = maxit; a.barrier_extra = extra;
+  a.timeout_ns = (unsigned long long)(b->timeout_ms * 1e6);
+  return a;
+}
+
+int read_error(fem_batch *b) {
+  BatchSync s;
+  FEM_CUDA_TRY(cudaMemcpyAsync(&s, b->d_sync, sizeof(s), cudaMemcpyDeviceToHost, b->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (s.error) {
+    BatchSync z = {0, 0, 0, 0};
+    FEM_CUDA_TRY(cudaMemcpyAsync(b->d_sync, &z, sizeof(z), cudaMemcpyHostToDevice, b->stream));
+    FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    fem_set_error("batch: a grid barrier of the persistent kernel timed out");
+    return FEM_ETIMEOUT;
+  }
+  return FEM_OK;
+}
+
+// Runs `steps` outer refinement steps (or until every problem converges).
+int run_solve(fem_batch *b, const fem_cg_opts *o, int *steps_out) {
+  const int g = b->ops[0]->nsm * 8;
+  BatchArgs a = args_of(b, o->maxit, 0);
+  std::vector<BatchScalars> h(b->n);
+  int steps = 0;
+  for (;;) {
+    batch_apply64_kernel<<<b->ops[0]->nsm * 4, kNT64, batch_smem<double, kNT64>(), b->stream>>>(a, b->d_gstart64);
+    FEM_CHECK_LAUNCH();
+    batch_residual_kernel<<<g, 256, 0, b->stream>>>(a);
+    FEM_CHECK_LAUNCH();
+    batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a, o->rtol * o->rtol,
+                                                                     o->inner_rtol * o->inner_rtol);
+    FEM_CHECK_LAUNCH();
+    int rc = launch_inner(b, a, b->nt_choice, b->bps);
+    if (rc) return rc;
+    batch_correct_kernel<<<g, 256, 0, b->stream>>>(a);
+    FEM_CHECK_LAUNCH();
+    batch_step_end_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a);
+    FEM_CHECK_LAUNCH();
+    rc = read_error(b);
+    if (rc) return rc;
+    FEM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_sc, sizeof(BatchScalars) * b->n,
+                                 cudaMemcpyDeviceToHost, b->stream));
+    FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    steps++;
+    bool all = true;
+    for (int i = 0; i < b->n; i++) all = all && h[i].converged;
+    if (all || steps > o->max_outer) break;
+  }
+  *steps_out = steps;
+  return FEM_OK;
+}
+
+}  // namespace
+
+extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **out) {
+  if (!out || !ops || n < 1 || n > 1024) { fem_set_error("fem_batch_create: need 1..1024 operators"); return FEM_EINVAL; }
+  *out = nullptr;
+  for (int i = 0; i < n; i++) {
+    const fem_op *op = ops[i];
+    if (!op || op->kind != FEM_DIFFUSION || op->quad != FEM_GAUSS || op->Q != op->P + 1 ||
+        !op->d_qdata32) {
+      fem_set_error("fem_batch_create: operator %d must be a FEM_F32 diffusion operator with "
+                    "Gauss q = p+2", i);
+      return FEM_EINVAL;
+    }
+    if (op->stream() != ops[0]->stream()) {
+      fem_set_error("fem_batch_create: all operators must share one stream");
+      return FEM_EINVAL;
+    }
+  }
+  fem_batch *b = new fem_batch();
+  b->n = n;
+  b->ops.assign(ops, ops + n);
+  b->stream = ops[0]->stream();
+  auto dalloc = [&](void **p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return false; }
+    b->allocs.push_back(*p);
+    b->bytes += (int64_t)bytes;
+    return true;
+  };
+  bool ok = dalloc((void **)&b->d_prob, sizeof(BatchProblem) * n) &&
+            dalloc((void **)&b->d_sc, sizeof(BatchScalars) * n) &&
+            dalloc((void **)&b->d_sync, sizeof(BatchSync)) &&
+            dalloc((void **)&b->d_gstart, sizeof(int64_t) * (n + 1)) &&
+            dalloc((void **)&b->d_gstart64, sizeof(int64_t) * (n + 1)) &&
+            dalloc((void **)&b->d_cstart, sizeof(int64_t) * (n + 1));
+  b->h_prob.resize(n);
+  std::vector<int64_t> cs(n + 1, 0), g64(n + 1, 0);
+  for (int i = 0; ok && i < n; i++) {
+    const fem_op *op = ops[i];
+    BatchProblem &p = b->h_prob[i];
+    p.P = op->P; p.Q = op->Q; p.ncomp = op->ncomp; p.N = op->N; p.E = op->E;
+    p.n = op->N * op->ncomp;
+    p.elem_nodes = op->mesh->d_elem_nodes; p.dir = op->mesh->d_dirichlet;
+    p.qdata32 = op->d_qdata32; p.B32 = op->d_B32; p.Dq32 = op->d_Dq32;
+    p.qdata64 = op->d_qdata; p.B64 = op->d_B; p.Dq64 = op->d_Dq;
+    p.diag = op->d_diag;
+    p.b = nullptr; p.x = nullptr;
+    const size_t nn = (size_t)p.n;
+    ok = dalloc((void **)&p.y64, 8 * nn) && dalloc((void **)&p.r, 4 * nn) &&
+         dalloc((void **)&p.z, 4 * nn) && dalloc((void **)&p.p, 4 * nn) &&
+         dalloc((void **)&p.y, 4 * nn) && dalloc((void **)&p.d, 4 * nn) &&
+         dalloc((void **)&p.dinv, 4 * nn);
+    cs[i + 1] = cs[i] + (p.n + kChunk - 1) / kChunk;
+    g64[i + 1] = g64[i] + groups_for(p, kNT64);
+  }
+  if (!ok) {
+    fem_set_error("fem_batch_create: device allocation failed");
+    fem_batch_destroy(b);
+    return FEM_ENOMEM;
+  }
+  b->n_chunks = cs[n];
+  b->n_items64 = g64[n];
+  cudaError_t e = cudaMemcpyAsync(b->d_cstart, cs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_gstart64, g64.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    fem_set_error("fem_batch_create: upload failed: %s", cudaGetErrorString(e));
+    fem_batch_destroy(b);
+    return FEM_ECUDA;
+  }
+  auto kern64 = batch_apply64_kernel;
+  if (cudaFuncSetAttribute(kern64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)batch_smem<double, kNT64>()) != cudaSuccess) {
+    fem_set_error("fem_batch_create: kernel attribute failed");
+    fem_batch_destroy(b);
+    return FEM_ECUDA;
+  }
+  int rc = build_items(b, kNtChoices[b->nt_choice]);
+  if (rc) { fem_batch_destroy(b); return rc; }
+  *out = b;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_batch_destroy(fem_batch *b) {
+  if (!b) return FEM_OK;
+  for (void *p : b->allocs) cudaFree(p);
+  delete b;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_batch_set_shape(fem_batch *b, int nt_choice, int blocks_per_sm,
+                                          double timeout_ms) {
+  if (!b || nt_choice < 0 || nt_choice > 2 || blocks_per_sm < 0 || !(timeout_ms > 0)) {
+    fem_set_error("fem_batch_set_shape: invalid arguments");
+    return FEM_EINVAL;
+  }
+  b->nt_choice = nt_choice;
+  b->bps = blocks_per_sm;
+  b->timeout_ms = timeout_ms;
+  return build_items(b, kNtChoices[nt_choice]);
+}
+
+static int bind_vectors(fem_batch *b, const double *const *bv, double *const *xv) {
+  for (int i = 0; i < b->n; i++) {
+    if (!bv[i] || !xv[i] || bv[i] == xv[i]) {
+      fem_set_error("fem_batch_solve: invalid vectors for problem %d", i);
+      return FEM_EINVAL;
+    }
+    b->h_prob[i].b = bv[i];
+    b->h_prob[i].x = xv[i];
+  }
+  FEM_CUDA_TRY(cudaMemcpyAsync(b->d_prob, b->h_prob.data(), sizeof(BatchProblem) * b->n,
+                               cudaMemcpyHostToDevice, b->stream));
+  return FEM_OK;
+}
+
+static int reset_scalars(fem_batch *b) {
+  std::vector<BatchScalars> z(b->n);
+  memset(z.data(), 0, sizeof(BatchScalars) * b->n);
+  FEM_CUDA_TRY(cudaMemcpyAsync(b->d_sc, z.data(), sizeof(BatchScalars) * b->n,
+                               cudaMemcpyHostToDevice, b->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_batch_solve(fem_batch *b, const double *const *bv, double *const *xv,
+                                      const fem_cg_opts *o, fem_cg_stats *stats) {
+  if (!b || !bv || !xv || !o) { fem_set_error("fem_batch_solve: invalid arguments"); return FEM_EINVAL; }
+  if (!(o->rtol > 0.0) || !(o->inner_rtol > 0.0) || o->maxit < 1 || o->max_outer < 1 ||
+      o->precond != FEM_PC_JACOBI) {
+    fem_set_error("fem_batch_solve: need Jacobi, rtol > 0, inner_rtol > 0, maxit >= 1, max_outer >= 1");
+    return FEM_EINVAL;
+  }
+  int rc = bind_vectors(b, bv, xv);
+  if (rc) return rc;
+  if ((rc = reset_scalars(b))) return rc;
+  BatchArgs a = args_of(b, o->maxit, 0);
+  batch_prepare_kernel<<<b->ops[0]->nsm * 8, 256, 0, b->stream>>>(a);
+  FEM_CHECK_LAUNCH();
+  int steps = 0;
+  rc = run_solve(b, o, &steps);
+  if (rc) return rc;
+  std::vector<BatchScalars> h(b->n);
+  FEM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_sc, sizeof(BatchScalars) * b->n,
+                               cudaMemcpyDeviceToHost, b->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  int status = FEM_OK;
+  for (int i = 0; i < b->n; i++) {
+    int st = h[i].status;
+    if (st == FEM_OK && !h[i].converged) st = FEM_ENOCONV;
+    if (stats) {
+      stats[i].iterations = h[i].total_iter;
+      stats[i].outer = h[i].outer;
+      stats[i].status = st;
+      stats[i].rnorm = sqrt(h[i].rr64_last);
+      stats[i].bnorm = sqrt(h[i].bb64_last);
+      stats[i].true_rel = h[i].bb64_last > 0 ? sqrt(h[i].rr64_last / h[i].bb64_last) : 0.0;
+    }
+    if (st != FEM_OK && status == FEM_OK) status = st;
+  }
+  return status;
+}
+
+// Test hook of the bounded grid barrier: launches the persistent kernel with
+// one arrival that never comes, so the first barrier must run out after
+// timeout_ms; returns what the host reads (FEM_ETIMEOUT).  The batch stays
+// usable afterwards.
+extern "C" fem_status fem_batch_barrier_selftest(fem_batch *b, double timeout_ms) {
+  if (!b || !(timeout_ms > 0) || b->h_prob[0].x == nullptr) {
+    fem_set_error("fem_batch_barrier_selftest: invalid arguments (solve once first)");
+    return FEM_EINVAL;
+  }
+  const double saved = b->timeout_ms;
+  b->timeout_ms = timeout_ms;
+  int rc = reset_scalars(b);
+  if (rc) { b->timeout_ms = saved; return rc; }
+  BatchArgs a = args_of(b, 1, 1u);
+  // problems active (done_at = INT_MAX) so that the kernel reaches a barrier
+  batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a, 0.0, 0.0);
+  FEM_CHECK_LAUNCH();
+  rc = launch_inner(b, a, b->nt_choice, b->bps);
+  b->timeout_ms = saved;
+  if (rc) return rc;
+  return read_error(b);
+}
+
+// Batch autotuner: time the persistent inner kernel's shapes (block size 128 /
+// 256 / 512, blocks per SM) on `iters` inner iterations of this batch from the
+// same start state, keep the fastest.  Needs the batch's vectors (b, x).
+extern "C" fem_status fem_batch_autotune(fem_batch *b, const double *const *bv,
+                                         double *const *xv, int iters, fem_tune_result *res) {
+  if (!b || !bv || !xv || iters < 1) { fem_set_error("fem_batch_autotune: invalid arguments"); return FEM_EINVAL; }
+  int rc = bind_vectors(b, bv, xv);
+  if (rc) return rc;
+  const int bps_cand[] = {1, 2, 0};
+  cudaEvent_t e0, e1;
+  FEM_CUDA_TRY(cudaEventCreate(&e0));
+  FEM_CUDA_TRY(cudaEventCreate(&e1));
+  double best = 1e300;
+  int best_nt = 1, best_bps = 0, ncand = 0;
+  for (int nt = 0; nt < 3 && rc == FEM_OK; nt++) {
+    if ((rc = build_items(b, kNtChoices[nt]))) break;
+    for (int bps : bps_cand) {
+      if ((rc = reset_scalars(b))) break;
+      BatchArgs a = args_of(b, iters, 0);
+      batch_prepare_kernel<<<b->ops[0]->nsm * 8, 256, 0, b->stream>>>(a);
+      batch_apply64_kernel<<<b->ops[0]->nsm * 4, kNT64, batch_smem<double, kNT64>(), b->stream>>>(a, b->d_gstart64);
+      batch_residual_kernel<<<b->ops[0]->nsm * 8, 256, 0, b->stream>>>(a);
+      batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a, 0.0, 0.0);
+      // keep every problem active for the timed iterations
+      std::vector<BatchScalars> h(b->n);
+      FEM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_sc, sizeof(BatchScalars) * b->n, cudaMemcpyDeviceToHost, b->stream));
+      FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+      for (auto &s : h) { s.converged = 0; s.done_at = INT_MAX; s.thresh = 0.0; }
+      FEM_CUDA_TRY(cudaMemcpyAsync(b->d_sc, h.data(), sizeof(BatchScalars) * b->n, cudaMemcpyHostToDevice, b->stream));
+      FEM_CUDA_TRY(cudaEventRecord(e0, b->stream));
+      if ((rc = launch_inner(b, a, nt, bps))) break;
+      FEM_CUDA_TRY(cudaEventRecord(e1, b->stream));
+      if ((rc = read_error(b))) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ncand++;
+      if (ms < best) { best = ms; best_nt = nt; best_bps = bps; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->nt_choice = best_nt;
+  b->bps = best_bps;
+  if ((rc = build_items(b, kNtChoices[best_nt]))) return rc;
+  if (res) {
+    res->epb_choice = best_nt; res->blocks_per_sm = best_bps; res->us = 1e3 * best / iters;
+    res->from_cache = 0; res->candidates = ncand;
+  }
+  return FEM_OK;
+}

@@ -99,6 +99,12 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   op->P = m->P; op->Q = q; op->N = m->N; op->E = m->E;
   op->colloc = (quad == FEM_LOBATTO && q == m->P);
   op->M = M; op->sigma = sigma;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&op->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (op->nsm < 1) op->nsm = 148;
+  }
   const int P = op->P, Q = op->Q;
   const int64_t Q3 = (int64_t)Q * Q * Q;
   const int nd = kind == FEM_DIFFUSION ? 6 : 1;

@@ -91,6 +91,9 @@ struct fem_op {
   double *d_partials = nullptr;   // [FEM_MAX_BLOCKS * 4]
   unsigned *d_counter = nullptr;  // [4]
   int64_t bytes = 0;
+  int nsm = 148;                  // SMs of the device the operator lives on
+  int tune_epb[2] = {0, 0};       // launch shape of the apply per precision:
+  int tune_bps[2] = {0, 0};       //   EPB choice index, blocks per SM (0 = max)
   CgWork *cg = nullptr;
   RefineWork *ir = nullptr;
   cudaStream_t stream() const { return mesh->stream; }
@@ -111,6 +114,11 @@ int fem_launch_apply_f64(fem_op *op, const double *x, double *y,
                          const int32_t *list, int64_t nsel, double *dot_out);
 int fem_launch_apply_f32(fem_op *op, const float *x, float *y,
                          const int32_t *list, int64_t nsel, double *dot_out);
+// explicit launch shape (autotuner): EPB choice index 0..2, blocks per SM (0 = max)
+int fem_launch_apply_f64_shape(fem_op *op, const double *x, double *y, const int32_t *list,
+                               int64_t nsel, double *dot_out, int choice, int bps);
+int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32_t *list,
+                               int64_t nsel, double *dot_out, int choice, int bps);
 // ---- setup (setup.cu)
 int fem_setup_qdata(fem_op *op);
 int fem_setup_diagonal(fem_op *op);

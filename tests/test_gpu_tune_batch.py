@@ -1,0 +1,142 @@
+"""GPU tests of the autotuner and of the batched persistent solve.
+
+Every launch shape of the apply must give the oracle's result (1e-12); a
+batch of problems of different order and size must give, per problem, the
+single-problem refined solve's result (same method, reduction order aside)
+and a true FP64 residual <= 1e-10 measured by the oracle.
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import fem_inputs
+import oracle
+import paper_2109_04996_b300 as fem
+from paper_2109_04996_b300 import build as fembuild
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    fembuild.build()
+    assert torch.cuda.is_available()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name,p,n", [("BP3", 3, 3), ("BP5", 7, 2), ("BP3", 8, 2)])
+@pytest.mark.parametrize("prec", [fem.F64, fem.F32])
+def test_every_launch_shape_matches_oracle(name, p, n, prec):
+    kind, ncomp, quad, dq = fem.BAKE_OFF[name]
+    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=2, shuffle_seed=9)
+    gm = fem.Mesh(m)
+    op = fem.Operator(gm, kind, quad, p + dq, prec=fem.F32)
+    orc = oracle.Operator(m, kind, quad, p + dq)
+    x = np.random.default_rng(1).uniform(-1, 1, m["N"])
+    ref = orc.apply(x)
+    tol = 1e-12 if prec == fem.F64 else 1e-5
+    for choice in range(3):
+        for bps in (1, 2, 0):
+            op.set_launch_shape(prec, choice, bps)
+            if prec == fem.F64:
+                y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+            else:
+                y = op.apply_f32(torch.from_numpy(x).float().cuda()).double().cpu().numpy()
+            assert rel(y, ref) <= tol, (choice, bps)
+
+
+def test_autotune_picks_a_shape_and_caches_it(tmp_path):
+    m = fem_inputs.box_mesh(6, 4, perturb=0.1, seed=3)
+    gm = fem.Mesh(m)
+    op = fem.Operator.bake_off(gm, "BP3", prec=fem.F32)
+    cache = str(tmp_path / "tune.json")
+    r1 = op.autotune(fem.F32, cache)
+    assert not r1["from_cache"] and r1["candidates"] >= 6 and r1["us"] > 0
+    import json
+    js = json.load(open(cache))
+    assert len(js["entries"]) == 1 and js["entries"][0]["epb_choice"] == r1["epb_choice"]
+    op2 = fem.Operator.bake_off(gm, "BP3", prec=fem.F32)
+    r2 = op2.autotune(fem.F32, cache)
+    assert r2["from_cache"] and r2["epb_choice"] == r1["epb_choice"]
+    assert r2["blocks_per_sm"] == r1["blocks_per_sm"]
+    r3 = op2.autotune(fem.F64, cache)           # a second key is appended
+    assert not r3["from_cache"]
+    assert len(json.load(open(cache))["entries"]) == 2
+    # the tuned operator still solves correctly
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=5)).cuda()
+    x = torch.zeros_like(b)
+    st = op2.cg(b, x, rtol=1e-10)
+    assert st["status"] == "FEM_OK"
+
+
+def _batch_problems(specs, ncomp=1):
+    out = []
+    for k, (n, p) in enumerate(specs):
+        m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=50 + k)
+        gm = fem.Mesh(m)
+        name = "BP3" if ncomp == 1 else "BP4"
+        op = fem.Operator.bake_off(gm, name, prec=fem.F32)
+        b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=60 + k,
+                                                    ncomp=ncomp)).cuda()
+        out.append((m, gm, op, b))
+    return out
+
+
+SPECS = [(4, 2), (2, 5), (3, 3), (2, 8), (5, 1), (3, 4), (2, 6), (2, 7)]
+
+
+def test_batch_matches_single_solves_and_oracle():
+    probs = _batch_problems(SPECS)
+    batch = fem.Batch([p[2] for p in probs])
+    xs = [torch.zeros_like(p[3]) for p in probs]
+    stats = batch.solve([p[3] for p in probs], xs, rtol=1e-10, inner_rtol=1e-5)
+    for (m, gm, op, b), x, st in zip(probs, xs, stats):
+        assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10, st
+        orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, m["p"] + 2)
+        bn = b.cpu().numpy()
+        inner = m["dirichlet"] == 0
+        res = np.where(inner, bn - orc.apply(x.cpu().numpy()), 0.0)
+        assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(bn)
+        xs1 = torch.zeros_like(b)
+        st1 = op.solve_refined(b, xs1, rtol=1e-10, inner_rtol=1e-5)
+        assert abs(st1["iterations"] - st["iterations"]) <= max(3, 0.05 * st1["iterations"])
+        assert st1["outer"] == st["outer"]
+        assert rel(x.cpu().numpy(), xs1.cpu().numpy()) <= 1e-8
+
+
+def test_batch_vector_problems_and_every_shape():
+    probs = _batch_problems([(3, 2), (2, 4), (2, 3)], ncomp=3)
+    batch = fem.Batch([p[2] for p in probs])
+    bs = [p[3] for p in probs]
+    for nt in range(3):
+        for bps in (1, 0):
+            batch.set_shape(nt, bps)
+            xs = [torch.zeros_like(b) for b in bs]
+            stats = batch.solve(bs, xs)
+            assert all(s["status"] == "FEM_OK" and s["true_rel"] <= 1e-10 for s in stats)
+    r = batch.autotune(bs, [torch.zeros_like(b) for b in bs], iters=5)
+    assert r["candidates"] == 9 and r["us_per_iter"] > 0
+    xs = [torch.zeros_like(b) for b in bs]
+    assert all(s["true_rel"] <= 1e-10 for s in batch.solve(bs, xs))
+
+
+def test_batch_barrier_runs_out_and_the_batch_stays_usable():
+    probs = _batch_problems([(3, 2), (2, 3)])
+    batch = fem.Batch([p[2] for p in probs])
+    bs = [p[3] for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch.solve(bs, xs)
+    t0 = time.perf_counter()
+    rc = batch.barrier_selftest(timeout_ms=200.0)
+    dt = time.perf_counter() - t0
+    assert rc == 6  # FEM_ETIMEOUT
+    assert dt < 10.0
+    xs = [torch.zeros_like(b) for b in bs]
+    stats = batch.solve(bs, xs)
+    assert all(s["status"] == "FEM_OK" and s["true_rel"] <= 1e-10 for s in stats)
