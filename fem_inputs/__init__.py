@@ -14,7 +14,7 @@ cube split into n^3 hexahedra whose interior vertices are moved by up to 0.1 h
 import numpy as np
 
 __all__ = ["box_mesh", "rhs_uniform", "rff_params", "elements_of_nodes",
-           "bp3_mesh_n", "batch_problems"]
+           "bp3_mesh_n", "batch_problems", "mlp_init"]
 
 
 def _rng(seed):
@@ -146,3 +146,16 @@ def batch_problems(count=64, seed=7, nmin=4, nmax=32, pmin=2, pmax=8):
     ps = rng.integers(pmin, pmax + 1, size=count)
     return [dict(n=int(ns[k]), p=int(ps[k]), mesh_seed=1000 + k, rhs_seed=2000 + k)
             for k in range(count)]
+
+
+def mlp_init(n_in, n_h, n_out, seed=0, out_scale=0.1):
+    """Initial weights of the per-element perceptron: He-uniform draws
+    U(-sqrt(6/fan_in), sqrt(6/fan_in)) (the last layer scaled by out_scale),
+    zero biases; flat float32 array in the order W1, b1, W2, b2, W3, b3."""
+    rng = _rng(seed)
+    parts = []
+    for fan_in, fan_out, sc in ((n_in, n_h, 1.0), (n_h, n_h, 1.0), (n_h, n_out, out_scale)):
+        lim = np.sqrt(6.0 / fan_in) * sc
+        parts.append(rng.uniform(-lim, lim, fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)

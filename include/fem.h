@@ -218,6 +218,8 @@ typedef struct {
   double rnorm;       /* final ||r||_2 of the recursive residual */
   double bnorm;       /* ||b||_2 over the unconstrained nodes */
   double true_rel;    /* refined: ||b - A_64 x|| / ||b|| in FP64 at exit */
+  int fallback;       /* fem_fcg_solve: 1 if the learned part was switched off
+                         (stagnation) and the solve finished with Jacobi */
 } fem_cg_stats;
 
 /* Preconditioned CG (section "Benchmarks": CG on the BP systems; diagonal
@@ -244,6 +246,78 @@ fem_status fem_cg_solve(fem_op *op, const double *b, double *x,
  * FEM_ENOCONV (max_outer reached) or FEM_EBREAKDOWN. */
 fem_status fem_solve_refined(fem_op *op, const double *b, double *x,
                              const fem_cg_opts *opts, fem_cg_stats *stats);
+
+/* Dirichlet-masked FP64 residual r = M (b - A x) (0 on constrained entries).
+ * b, x, r: device [ncomp*N]; r must not alias b or x. */
+fem_status fem_op_residual(fem_op *op, const double *b, const double *x,
+                           double *r);
+
+/* ---------------------------------------------------------------- learned preconditioner */
+
+/* A per-element multilayer perceptron and its training (the paper has none;
+ * its preconditioning material is the section "Ecosystem").  Network:
+ *   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), y = h2 W3^T + b3,
+ * x in R^n_in, hidden width n_h, y in R^n_out (all multiples of 32).
+ * Parameters: one FP32 array in the order W1 [n_h][n_in], b1, W2 [n_h][n_h],
+ * b2, W3 [n_out][n_h], b3 (FP32 masters, Adam moments on the device).
+ * mode 0: GEMMs in bf16 on the tensor cores (mma.sync) with FP32
+ * accumulation, activations in bf16; mode 1: all FP32 (reference/debug).
+ * Row inputs X are bf16 (mode 0) or FP32 (mode 1), row-major [rows][n_in]. */
+typedef struct fem_mlp fem_mlp;
+fem_status fem_mlp_create(int n_in, int n_h, int n_out, int mode,
+                          const float *params_host, void *stream, fem_mlp **out);
+fem_status fem_mlp_destroy(fem_mlp *mlp);
+/* Current parameters to host (params_host may be NULL) and their count. */
+fem_status fem_mlp_params(fem_mlp *mlp, float *params_host, int64_t *count);
+/* Y [rows][n_out] FP32 = network(X). */
+fem_status fem_mlp_forward(fem_mlp *mlp, const void *X, int64_t rows, float *Y);
+/* One Adam step (lr; b1 = 0.9, b2 = 0.999, eps = 1e-8) on the loss
+ * (1/S) sum_rows ||y[:valid] - T[:valid]||^2 over S rows (a multiple of 32).
+ * grad_host != NULL: copy the FP32 gradient out and do NOT update.
+ * loss_host: the loss before the step.  Synchronizes. */
+fem_status fem_mlp_train_step(fem_mlp *mlp, const void *X, const float *T,
+                              int64_t S, int valid, float lr, float *grad_host,
+                              double *loss_host);
+/* Minibatch training: `epochs` passes over S rows in seeded random order,
+ * floor(S/batch) Adam steps each; loss_host[epochs] = mean loss per epoch. */
+fem_status fem_mlp_train(fem_mlp *mlp, const void *X, const float *T, int64_t S,
+                         int valid, int epochs, int batch, float lr,
+                         uint64_t seed, double *loss_host);
+
+/* The learned preconditioner of a scalar FEM_F32 operator:
+ *   z = dinv * r + sum_e G_e^T ( w * ||r_e|| * net([r_e / ||r_e||, g_e]) )
+ * g_e: 32 element features (the 8 corner nodes' offsets from the centroid
+ * divided by the element size, then log kappa at the corners); w = 1 / node
+ * multiplicity.  mlp == NULL gives the Jacobi part alone.  The network needs
+ * n_in >= (p+1)^3 + 32 and n_out >= (p+1)^3; both must outlive the
+ * preconditioner. */
+typedef struct fem_precond fem_precond;
+fem_status fem_precond_create(fem_op *op, fem_mlp *mlp, fem_precond **out);
+fem_status fem_precond_destroy(fem_precond *pc);
+/* Element features [E][32] to host. */
+fem_status fem_precond_features(fem_precond *pc, float *feat_host);
+/* Training rows (E of them) from an iterate x_k of the plain solver for the
+ * right-hand side b whose solution is x_star (device FP64 [N] each): with
+ * r = M (b - A x_k) and e = x_star - x_k, per element
+ * X = [r_e / ||r_e||, g_e, 0...] (network input type) and
+ * T = [e_e / ||r_e||, 0...] (FP32, n_out wide). */
+fem_status fem_precond_samples(fem_precond *pc, const double *b,
+                               const double *x_star, const double *x_k,
+                               void *X, float *T);
+/* Weight gamma >= 0 of the learned correction in B (default 1; 0 = Jacobi
+ * alone, the network is then skipped). */
+fem_status fem_precond_set_gamma(fem_precond *pc, double gamma);
+/* z = B(r) (device FP32 [N] each). */
+fem_status fem_precond_apply(fem_precond *pc, const float *r, float *z);
+/* Flexible CG (Notay 2000, one stored direction) with preconditioner B as
+ * the inner FP32 solve of FP64 iterative refinement (as fem_solve_refined).
+ * Each outer step is one CUDA graph; the learned correction sits in a
+ * conditional IF node.  Fallback: every 64 inner iterations the residual
+ * must have dropped 4x, else the learned part is switched off for the rest
+ * of the solve (stats->fallback = 1), which then is Jacobi-PCG.  opts: rtol,
+ * inner_rtol, maxit, max_outer (precond is implied).  Synchronizes. */
+fem_status fem_fcg_solve(fem_precond *pc, const double *b, double *x,
+                         const fem_cg_opts *opts, fem_cg_stats *stats);
 
 /* ---------------------------------------------------------------- batches */
 

@@ -58,6 +58,16 @@ def lib():
         L.oracle_kappa.restype = ctypes.c_double
         L.oracle_kappa.argtypes = [ctypes.c_void_p, dp]
         L.oracle_max_threads.restype = ctypes.c_int
+        L.oracle_mlp_nparams.restype = ctypes.c_int64
+        L.oracle_mlp_nparams.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.oracle_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                         ctypes.c_int, dp, dp, dp, dp]
+        L.oracle_mlp_loss_grad.restype = ctypes.c_double
+        L.oracle_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                           ctypes.c_int, dp, dp, dp]
+        L.oracle_adam_step.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double]
         _lib = L
     return _lib
 
@@ -279,3 +289,37 @@ def pcg(op, b, dirichlet, rtol=1e-10, maxit=10000, precond="jacobi", x0=None):
 
 def max_threads():
     return lib().oracle_max_threads()
+
+
+# ---------------------------------------------------------------- MLP (oracle/mlp.c)
+
+def mlp_nparams(n_in, n_h, n_out):
+    return lib().oracle_mlp_nparams(n_in, n_h, n_out)
+
+
+def mlp_forward(dims, params, x):
+    """FP64 forward of the 3-layer ReLU perceptron; returns (y, h1, h2)."""
+    n_in, n_h, n_out = dims
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    S = x.shape[0]
+    y = np.zeros((S, n_out)); h1 = np.zeros((S, n_h)); h2 = np.zeros((S, n_h))
+    lib().oracle_mlp_forward(n_in, n_h, n_out, _dp(p), S, _dp(x), _dp(y), _dp(h1), _dp(h2))
+    return y, h1, h2
+
+
+def mlp_loss_grad(dims, params, x, t):
+    """L = mean over rows of ||y - t||^2 and dL/dparams (FP64)."""
+    n_in, n_h, n_out = dims
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    g = np.zeros_like(p)
+    L = lib().oracle_mlp_loss_grad(n_in, n_h, n_out, _dp(p), x.shape[0], _dp(x), _dp(t), _dp(g))
+    return L, g
+
+
+def adam_step(params, grad, m, v, k, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step k (>= 1) on FP64 arrays."""
+    lib().oracle_adam_step(params.size, _dp(params), _dp(np.ascontiguousarray(grad)), _dp(m),
+                           _dp(v), k, lr, b1, b2, eps)

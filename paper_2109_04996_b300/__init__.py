@@ -51,7 +51,7 @@ class _CgOpts(ctypes.Structure):
 class _CgStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("status", ctypes.c_int),
                 ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
-                ("true_rel", ctypes.c_double)]
+                ("true_rel", ctypes.c_double), ("fallback", ctypes.c_int)]
 
 
 _lib = None
@@ -87,6 +87,23 @@ def lib():
         "fem_solve_refined": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_op_set_launch_shape": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "fem_op_autotune": [_VP, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(_TuneResult)],
+        "fem_op_residual": [_VP, _VP, _VP, _VP],
+        "fem_mlp_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                           ctypes.POINTER(_VP)],
+        "fem_mlp_destroy": [_VP],
+        "fem_mlp_params": [_VP, _VP, ctypes.POINTER(ctypes.c_int64)],
+        "fem_mlp_forward": [_VP, _VP, _I64, _VP],
+        "fem_mlp_train_step": [_VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_float, _VP,
+                               ctypes.POINTER(ctypes.c_double)],
+        "fem_mlp_train": [_VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_float, ctypes.c_uint64, _VP],
+        "fem_precond_create": [_VP, _VP, ctypes.POINTER(_VP)],
+        "fem_precond_destroy": [_VP],
+        "fem_precond_features": [_VP, _VP],
+        "fem_precond_samples": [_VP, _VP, _VP, _VP, _VP, _VP],
+        "fem_precond_apply": [_VP, _VP, _VP],
+        "fem_precond_set_gamma": [_VP, ctypes.c_double],
+        "fem_fcg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_batch_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
         "fem_batch_destroy": [_VP],
         "fem_batch_solve": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
@@ -255,6 +272,14 @@ class Operator:
             _check(rc)
         return _stats(st)
 
+    def residual(self, b, x, r=None):
+        """r = M (b - A x) in FP64 (Dirichlet entries 0)."""
+        import torch
+        if r is None:
+            r = torch.empty_like(x)
+        _check(lib().fem_op_residual(self._h, _ptr(b), _ptr(x), _ptr(r)))
+        return r
+
     def set_launch_shape(self, prec, epb_choice, blocks_per_sm=0):
         _check(lib().fem_op_set_launch_shape(self._h, prec, epb_choice, blocks_per_sm))
 
@@ -281,7 +306,7 @@ class Operator:
 
 def _stats(st):
     return dict(iterations=st.iterations, outer=st.outer, status=STATUS[st.status],
-                rnorm=st.rnorm, bnorm=st.bnorm, true_rel=st.true_rel)
+                rnorm=st.rnorm, bnorm=st.bnorm, true_rel=st.true_rel, fallback=st.fallback)
 
 
 class Batch:
@@ -328,3 +353,119 @@ class Batch:
         """Status code returned when the persistent kernel's barrier is made
         to wait for an arrival that never comes (FEM_ETIMEOUT expected)."""
         return lib().fem_batch_barrier_selftest(self._h, timeout_ms)
+
+
+class Mlp:
+    """Per-element perceptron n_in -> n_h -> n_h -> n_out (ReLU), FP32 master
+    weights; mode 0 = bf16 tensor-core GEMMs, 1 = FP32 (fem_mlp_*)."""
+
+    def __init__(self, n_in, n_h, n_out, params, mode=0, stream=None):
+        self.n_in, self.n_h, self.n_out, self.mode = n_in, n_h, n_out, mode
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        h = _VP()
+        _check(lib().fem_mlp_create(n_in, n_h, n_out, mode, _ptr(p), _stream_handle(stream),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fem_mlp_destroy(self._h)
+            self._h = None
+
+    @property
+    def input_dtype(self):
+        import torch
+        return torch.bfloat16 if self.mode == 0 else torch.float32
+
+    def params(self):
+        n = ctypes.c_int64()
+        _check(lib().fem_mlp_params(self._h, None, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.float32)
+        _check(lib().fem_mlp_params(self._h, _ptr(out), ctypes.byref(n)))
+        return out
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty(X.shape[0], self.n_out, dtype=torch.float32, device=X.device)
+        _check(lib().fem_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Y)))
+        return Y
+
+    def gradient(self, X, T, valid):
+        """(loss, FP32 gradient) without updating."""
+        g = np.zeros(self.params().size, dtype=np.float32)
+        L = ctypes.c_double()
+        _check(lib().fem_mlp_train_step(self._h, _ptr(X), _ptr(T), X.shape[0], valid, 0.0,
+                                        _ptr(g), ctypes.byref(L)))
+        return L.value, g
+
+    def step(self, X, T, valid, lr):
+        L = ctypes.c_double()
+        _check(lib().fem_mlp_train_step(self._h, _ptr(X), _ptr(T), X.shape[0], valid, lr, None,
+                                        ctypes.byref(L)))
+        return L.value
+
+    def train(self, X, T, valid, epochs, batch=4096, lr=1e-3, seed=0):
+        losses = np.zeros(epochs)
+        _check(lib().fem_mlp_train(self._h, _ptr(X), _ptr(T), X.shape[0], valid, epochs, batch,
+                                   lr, seed, _ptr(losses)))
+        return losses
+
+
+class Precond:
+    """Jacobi + learned per-element correction (fem_precond_*); mlp=None
+    gives the Jacobi part alone."""
+
+    def __init__(self, op, mlp=None):
+        self.op, self.mlp = op, mlp
+        h = _VP()
+        _check(lib().fem_precond_create(op._h, None if mlp is None else mlp._h, ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fem_precond_destroy(self._h)
+            self._h = None
+
+    def features(self):
+        out = np.zeros((self.op.E, 32), dtype=np.float32)
+        _check(lib().fem_precond_features(self._h, _ptr(out)))
+        return out
+
+    def samples(self, b, x_star, x_k, X, T):
+        _check(lib().fem_precond_samples(self._h, _ptr(b), _ptr(x_star), _ptr(x_k), _ptr(X),
+                                         _ptr(T)))
+
+    def set_gamma(self, gamma):
+        _check(lib().fem_precond_set_gamma(self._h, float(gamma)))
+        self.gamma = float(gamma)
+
+    def calibrate(self, b, gammas=(1.0, 0.5, 0.25, 0.1, 0.0), probe_iters=64):
+        """Pick the learned-term weight: for each candidate, run `probe_iters`
+        FCG iterations on right-hand side b from x = 0 and keep the weight
+        with the smallest true residual (0 = Jacobi alone)."""
+        import torch
+        best = None
+        for gm in gammas:
+            self.set_gamma(gm)
+            x = torch.zeros_like(b)
+            st = self.fcg(b, x, rtol=1e-14, inner_rtol=1e-14, maxit=probe_iters, max_outer=1)
+            score = st["true_rel"] if st["fallback"] == 0 else float("inf")
+            if best is None or score < best[1]:
+                best = (gm, score)
+        self.set_gamma(best[0])
+        return best[0]
+
+    def apply(self, r):
+        import torch
+        z = torch.empty_like(r)
+        _check(lib().fem_precond_apply(self._h, _ptr(r), _ptr(z)))
+        return z
+
+    def fcg(self, b, x, rtol=1e-10, inner_rtol=1e-5, maxit=100000, max_outer=20):
+        o = _CgOpts(PC_LEARNED, int(maxit), float(rtol), 1, float(inner_rtol), int(max_outer))
+        st = _CgStats()
+        rc = lib().fem_fcg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        if rc not in (0, 5):
+            _check(rc)
+        return _stats(st)
+

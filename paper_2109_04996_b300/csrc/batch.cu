@@ -658,6 +658,7 @@ extern "C" fem_status fem_batch_solve(fem_batch *b, const double *const *bv, dou
       stats[i].rnorm = sqrt(h[i].rr64_last);
       stats[i].bnorm = sqrt(h[i].bb64_last);
       stats[i].true_rel = h[i].bb64_last > 0 ? sqrt(h[i].rr64_last / h[i].bb64_last) : 0.0;
+      stats[i].fallback = 0;
     }
     if (st != FEM_OK && status == FEM_OK) status = st;
   }

@@ -242,3 +242,24 @@ extern "C" fem_status fem_cg_solve(fem_op *op, const double *b, double *x, const
   return fem_cg_run(op, b, x, o, st);
 }
 
+
+namespace {
+__global__ void residual_kernel(const double *b, double *r, const uint8_t *dir, int64_t N, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = (dir && dir[i % N]) ? 0.0 : b[i] - r[i];
+}
+}  // namespace
+
+extern "C" fem_status fem_op_residual(fem_op *op, const double *b, const double *x, double *r) {
+  if (!op || !b || !x || !r || r == x || r == b) {
+    fem_set_error("fem_op_residual: invalid arguments");
+    return FEM_EINVAL;
+  }
+  int rc = fem_op_apply(op, x, r);
+  if (rc) return rc;
+  const int64_t n = op->N * op->ncomp;
+  residual_kernel<<<148 * 8, 256, 0, op->stream()>>>(b, r, op->mesh->d_dirichlet, op->N, n);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}

@@ -341,6 +341,7 @@ int fem_cg_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
     st->rnorm = sqrt(out.rr);
     st->bnorm = sqrt(out.bb);
     st->true_rel = -1.0;
+    st->fallback = 0;
   }
   return out.status;
 }
@@ -479,6 +480,7 @@ extern "C" fem_status fem_cg_solve_noalloc(fem_op *op, const double *b, double *
     st->rnorm = sqrt(out.rr);
     st->bnorm = sqrt(out.bb);
     st->true_rel = -1.0;
+    st->fallback = 0;
   }
   return out.status;
 }

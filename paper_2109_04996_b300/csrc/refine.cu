@@ -346,6 +346,7 @@ extern "C" fem_status fem_solve_refined(fem_op *op, const double *b, double *x,
     st->rnorm = sqrt(out.rr64);
     st->bnorm = sqrt(out.bb64);
     st->true_rel = out.bb64 > 0 ? sqrt(out.rr64 / out.bb64) : 0.0;
+    st->fallback = 0;
   }
   return status;
 }

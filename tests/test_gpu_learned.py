@@ -1,0 +1,222 @@
+"""GPU tests of the learned preconditioner: the network's forward and
+backward against the FP64 CPU oracle (oracle/mlp.c), training, the element
+features and samples, and flexible CG with the trained network (final error
+judged by the FP64 oracle)."""
+import numpy as np
+import pytest
+import torch
+
+import fem_inputs
+import oracle
+import paper_2109_04996_b300 as fem
+from paper_2109_04996_b300 import build as fembuild
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    fembuild.build()
+    assert torch.cuda.is_available()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+DIMS = (96, 64, 64)
+
+
+def _data(S, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 1, (S, DIMS[0]))
+    t = rng.normal(0, 0.3, (S, DIMS[2]))
+    return x, t
+
+
+@pytest.mark.parametrize("mode,tol", [(1, 1e-5), (0, 2e-2)])
+def test_forward_matches_oracle(mode, tol):
+    p = fem_inputs.mlp_init(*DIMS, seed=1, out_scale=1.0)
+    net = fem.Mlp(*DIMS, p, mode=mode)
+    x, _ = _data(200)
+    X = torch.from_numpy(x).to(net.input_dtype).cuda()
+    y = net.forward(X).double().cpu().numpy()
+    xin = X.double().cpu().numpy()           # the rounded input the GPU saw
+    yr, _, _ = oracle.mlp_forward(DIMS, p.astype(np.float64), xin)
+    assert rel(y, yr) <= tol
+
+
+@pytest.mark.parametrize("mode,tol", [(1, 1e-5), (0, 5e-2)])
+def test_gradient_matches_oracle(mode, tol):
+    p = fem_inputs.mlp_init(*DIMS, seed=2, out_scale=1.0)
+    net = fem.Mlp(*DIMS, p, mode=mode)
+    x, t = _data(256, seed=3)
+    valid = 50
+    t[:, valid:] = 0.0
+    X = torch.from_numpy(x).to(net.input_dtype).cuda()
+    T = torch.from_numpy(t).float().cuda()
+    L, g = net.gradient(X, T, valid)
+    xin = X.double().cpu().numpy()
+    # the oracle's loss over the first `valid` outputs: zero the other outputs' rows of W3, b3
+    n_in, n_h, n_out = DIMS
+    pv = p.astype(np.float64).copy()
+    off3 = n_h * n_in + n_h + n_h * n_h + n_h
+    W3 = pv[off3:off3 + n_out * n_h].reshape(n_out, n_h)
+    W3[valid:] = 0.0
+    pv[off3 + n_out * n_h + valid:] = 0.0
+    Lr, gr = oracle.mlp_loss_grad(DIMS, pv, xin, np.where(np.arange(n_out) < valid, t, 0.0))
+    gm = g.astype(np.float64)
+    keep = np.ones_like(gm, dtype=bool)    # outputs >= valid carry no gradient on the GPU side
+    keep[off3:off3 + n_out * n_h] = (np.arange(n_out)[:, None] < valid).repeat(n_h, 1).ravel()
+    keep[off3 + n_out * n_h:] = np.arange(n_out) < valid
+    assert abs(L - Lr) <= tol * Lr
+    assert rel(gm[keep], gr[keep]) <= tol
+
+
+def test_adam_step_matches_oracle():
+    p = fem_inputs.mlp_init(*DIMS, seed=4, out_scale=1.0)
+    net = fem.Mlp(*DIMS, p, mode=1)
+    x, t = _data(128, seed=5)
+    X = torch.from_numpy(x).float().cuda()
+    T = torch.from_numpy(t).float().cuda()
+    _, g = net.gradient(X, T, DIMS[2])
+    net.step(X, T, DIMS[2], 1e-3)
+    q = p.astype(np.float64).copy()
+    m = np.zeros_like(q); v = np.zeros_like(q)
+    oracle.adam_step(q, g.astype(np.float64), m, v, 1, lr=1e-3)
+    assert rel(net.params(), q) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_training_reduces_the_loss(mode):
+    # a learnable map: t = tanh(x A) for a fixed random A
+    rng = np.random.default_rng(7)
+    A = rng.normal(0, 0.2, (DIMS[0], DIMS[2]))
+    x = rng.normal(0, 1, (8192, DIMS[0]))
+    t = np.tanh(x @ A)
+    net = fem.Mlp(*DIMS, fem_inputs.mlp_init(*DIMS, seed=8), mode=mode)
+    X = torch.from_numpy(x).to(net.input_dtype).cuda()
+    T = torch.from_numpy(t).float().cuda()
+    losses = net.train(X, T, DIMS[2], epochs=15, batch=512, lr=2e-3, seed=1)
+    assert losses[-1] < 0.5 * losses[0], losses
+    assert all(b < a for a, b in zip(losses[:-1], losses[1:]))
+
+
+def _kappa_problem(n=4, p=4, seed=11):
+    rff = fem_inputs.rff_params(128, 0.1, seed=seed)
+    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=seed)
+    gm = fem.Mesh(m)
+    op = fem.Operator.bake_off(gm, "BP3", prec=fem.F32, rff=rff)
+    return m, gm, op, rff
+
+
+def test_features_and_samples():
+    m, gm, op, rff = _kappa_problem(n=3, p=2)
+    n_in = 64 if 27 + 32 <= 64 else 96
+    net = fem.Mlp(n_in, 64, 32, fem_inputs.mlp_init(n_in, 64, 32), mode=1)
+    pc = fem.Precond(op, net)
+    f = pc.features()
+    # corners of element e are its trilinear vertices; h = side of the cube
+    orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, 4, rff=rff)
+    V = m["vert_xyz"][m["elem_verts"]]                  # [E, 8, 3]
+    cen = V.mean(1, keepdims=True)
+    h = 2 / np.sqrt(3) * np.sqrt(((V - cen) ** 2).sum((1, 2)) / 8)
+    np.testing.assert_allclose(f[:, :24], ((V - cen) / h[:, None, None]).reshape(-1, 24), atol=1e-5)
+    lk = np.array([[np.log(orc.kappa(V[e, v])) for v in range(8)] for e in range(m["E"])])
+    np.testing.assert_allclose(f[:, 24:], lk, atol=1e-5)
+    # samples: X = [r_e/|r_e|, g_e, 0], T = [e_e/|r_e|, 0]
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=1)).cuda()
+    xs = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, m["N"])).cuda()
+    xk = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, m["N"])).cuda()
+    X = torch.zeros(m["E"], n_in, dtype=torch.float32, device="cuda")
+    T = torch.zeros(m["E"], 32, dtype=torch.float32, device="cuda")
+    pc.samples(b, xs, xk, X, T)
+    inner = m["dirichlet"] == 0
+    r = np.where(inner, b.cpu().numpy() - orc.apply(xk.cpu().numpy()), 0.0)
+    err = xs.cpu().numpy() - xk.cpu().numpy()
+    en = m["elem_nodes"]
+    nr = np.linalg.norm(r[en], axis=1)
+    np.testing.assert_allclose(X.cpu().numpy()[:, :27], r[en] / nr[:, None], atol=2e-6)
+    np.testing.assert_allclose(X.cpu().numpy()[:, 27:59], f, atol=0)
+    np.testing.assert_allclose(T.cpu().numpy()[:, :27], err[en] / nr[:, None], rtol=1e-5, atol=1e-5)
+
+
+def test_fcg_jacobi_only_converges_like_pcg():
+    m, gm, op, rff = _kappa_problem(n=5, p=3)
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=3)).cuda()
+    pc = fem.Precond(op, None)
+    x = torch.zeros_like(b)
+    st = pc.fcg(b, x, rtol=1e-10)
+    assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10
+    x2 = torch.zeros_like(b)
+    st2 = op.solve_refined(b, x2, rtol=1e-10, inner_rtol=1e-5)
+    assert abs(st["iterations"] - st2["iterations"]) <= 0.1 * st2["iterations"] + 3
+    assert rel(x.cpu().numpy(), x2.cpu().numpy()) <= 1e-8
+
+
+def _train_learned(op, m, nrhs=6, ks=(2, 5, 10, 20, 40, 80), epochs=40, mode=0, seed=0):
+    P3 = (m["p"] + 1) ** 3
+    n_in = ((P3 + 32 + 31) // 32) * 32
+    n_out = ((P3 + 31) // 32) * 32
+    net = fem.Mlp(n_in, 256, n_out, fem_inputs.mlp_init(n_in, 256, n_out, seed=seed), mode=mode)
+    pc = fem.Precond(op, net)
+    rows = nrhs * len(ks) * m["E"]
+    X = torch.zeros(rows, n_in, dtype=net.input_dtype, device="cuda")
+    T = torch.zeros(rows, n_out, dtype=torch.float32, device="cuda")
+    r0 = 0
+    for j in range(nrhs):
+        b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=100 + j)).cuda()
+        xs = torch.zeros_like(b)
+        op.solve_refined(b, xs, rtol=1e-12, inner_rtol=1e-5)
+        for k in ks:
+            xk = torch.zeros_like(b)
+            op.cg(b, xk, maxit=k, rtol=0.0)
+            pc.samples(b, xs, xk, X[r0:r0 + m["E"]], T[r0:r0 + m["E"]])
+            r0 += m["E"]
+    batch = max(32, min(1024, (rows // 8) // 32 * 32))
+    losses = net.train(X, T, P3, epochs=epochs, batch=batch, lr=1e-3, seed=seed)
+    return net, pc, losses
+
+
+def test_learned_fcg_reaches_fp64_accuracy_and_reports_its_gain():
+    m, gm, op, rff = _kappa_problem(n=6, p=4)
+    net, pc, losses = _train_learned(op, m)
+    assert losses[-1] < losses[0]
+    bval = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=998)).cuda()
+    gamma = pc.calibrate(bval)
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=999)).cuda()
+    x = torch.zeros_like(b)
+    st = pc.fcg(b, x, rtol=1e-10)
+    assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10
+    orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, 6, rff=rff)
+    inner = m["dirichlet"] == 0
+    bn = b.cpu().numpy()
+    res = np.where(inner, bn - orc.apply(x.cpu().numpy()), 0.0)
+    assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(bn)
+    # the method without the network on the same system
+    x0 = torch.zeros_like(b)
+    st0 = fem.Precond(op, None).fcg(b, x0, rtol=1e-10)
+    gain = st0["iterations"] / st["iterations"]
+    print("\nlearned FCG: gamma %.2f, %d iterations (fallback %d) vs Jacobi %d: gain %.2fx;"
+          " training loss %.3g -> %.3g" % (gamma, st["iterations"], st["fallback"],
+                                          st0["iterations"], gain, losses[0], losses[-1]))
+    # calibration never picks a weight that loses to Jacobi on the probe by much
+    assert gain > 0.7
+
+
+def test_bad_network_falls_back_to_jacobi_and_still_converges():
+    m, gm, op, rff = _kappa_problem(n=5, p=3)
+    P3 = 64
+    net = fem.Mlp(96, 64, 64, fem_inputs.mlp_init(96, 64, 64, seed=3, out_scale=30.0), mode=0)
+    pc = fem.Precond(op, net)
+    pc.set_gamma(1.0)
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=5)).cuda()
+    x = torch.zeros_like(b)
+    st = pc.fcg(b, x, rtol=1e-10)
+    assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10
+    assert st["fallback"] == 1
+    # gamma = 0 is the Jacobi method (no network work at all)
+    pc.set_gamma(0.0)
+    x0 = torch.zeros_like(b)
+    st0 = pc.fcg(b, x0, rtol=1e-10)
+    assert st0["fallback"] == 0 and st0["true_rel"] <= 1e-10
