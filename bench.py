@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--tts-dofs", type=float, default=1e7,
                     help="size of the time-to-1e-10 comparison (0 = skip)")
     ap.add_argument("--tts-order", type=int, default=4)
+    ap.add_argument("--sections", default="bp56,batched,learned",
+                    help="extra measured configurations: bp56, batched, learned (comma list)")
+    ap.add_argument("--bp56-n", type=int, default=44, help="elements per direction, BP5/BP6 p=7")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--learned-n", type=int, default=64, help="elements per direction, kappa BP3 p=4")
     return ap.parse_args()
 
 
@@ -228,6 +233,211 @@ def time_to_solution(fem, torch, args):
     return out
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _time_apply(torch, fn, reps=5, warm=3):
+    for _ in range(warm):
+        fn()
+    a0, a1 = _events()
+    a0.record()
+    for _ in range(reps):
+        fn()
+    a1.record()
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / reps * 1e-3
+
+
+def section_bp56(fem, torch, args):
+    """BP5 (scalar) and BP6 (3 components) diffusion, Gauss-Lobatto q=p+1,
+    p=7: FP64 and FP32 apply throughput with the FP32 kernel's HBM roofline,
+    FP32 apply error against the FP64 oracle on sampled rows, and the time to
+    a 1e-10 FP64 residual of plain FP64 PCG vs FP32 PCG + FP64 refinement."""
+    import oracle
+    p, n = 7, args.bp56_n
+    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=500)
+    gm = fem.Mesh(m)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    out = {"mesh": "p=7 n=%d N=%d per component" % (n, m["N"])}
+    rows = np.random.default_rng(5).choice(m["N"], 200, replace=False)
+    rows = rows[m["dirichlet"][rows] == 0]
+    ptr, rel_el = fem_inputs.elements_of_nodes(m, rows)
+    orc = oracle.Operator(m, oracle.DIFFUSION, oracle.LOBATTO, p + 1)
+    for name in ("BP5", "BP6"):
+        op = fem.Operator.bake_off(gm, name, prec=fem.F32)
+        nc = op.ncomp
+        N, E = m["N"], m["E"]
+        x = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, nc * N)).cuda()
+        y = torch.empty_like(x)
+        x32, y32 = x.float(), torch.empty(nc * N, dtype=torch.float32, device="cuda")
+        t64 = _time_apply(torch, lambda: op.apply(x, y))
+        t32 = _time_apply(torch, lambda: op.apply_f32(x32, y32))
+        P, q = p + 1, p + 1
+        by64 = nc * 16 * N + 4 * E * P ** 3 + 48 * E * q ** 3
+        by32 = nc * 8 * N + 4 * E * P ** 3 + 24 * E * q ** 3
+        fl = nc * E * (12 * P ** 4 + 18 * P ** 3)
+        # sampled-row error of the FP32 apply (component 0) against the oracle
+        ys = y32[:N].double().cpu().numpy()[rows]
+        yr = orc.apply_rows(x[:N].cpu().numpy(), rows, ptr, rel_el)
+        err32 = float(np.linalg.norm(ys - yr) / np.linalg.norm(yr))
+        b = torch.from_numpy(fem_inputs.rhs_uniform(N, m["dirichlet"], seed=600, ncomp=nc)).cuda()
+        tts = {}
+        for meth in ("fp64_pcg", "fp32_refined"):
+            best = None
+            for _ in range(2):
+                xs = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = (op.cg(b, xs, rtol=1e-10) if meth == "fp64_pcg"
+                      else op.solve_refined(b, xs, rtol=1e-10, inner_rtol=1e-5))
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+                best = t if best is None else min(best, t)
+            r = op.residual(b, xs)
+            tts[meth] = {"seconds": best, "iterations": st["iterations"],
+                         "true_rel_residual": (torch.linalg.norm(r) / torch.linalg.norm(b)).item()}
+        out[name] = {
+            "dofs": nc * N,
+            "apply_f64": {"ms": t64 * 1e3, "gdofs": nc * N / t64 / 1e9, "tflops": fl / t64 / 1e12},
+            "apply_f32": {"ms": t32 * 1e3, "gdofs": nc * N / t32 / 1e9,
+                          "hbm_gbs": by32 / t32 / 1e9, "hbm_frac_of_measured": by32 / t32 / 1e9 / hbm,
+                          "algorithmic_bytes": by32, "tflops": fl / t32 / 1e12},
+            "apply_f32_rel_error_vs_oracle": err32,
+            "time_to_1e-10": tts,
+            "speedup_refined_vs_fp64": tts["fp64_pcg"]["seconds"] / tts["fp32_refined"]["seconds"]}
+        del op, x, y, x32, y32, b
+    return out
+
+
+def section_batched(fem, torch, args):
+    """64 independent BP3 problems (n in 4..32, p in 2..8 from seed 7), FP32
+    operators with FP64 refinement, all inner iterations in one persistent
+    kernel per outer step, autotuned block shape; vs the same problems solved
+    one after another with fem_solve_refined."""
+    specs = fem_inputs.batch_problems(args.batch_count, seed=7)
+    probs = []
+    for s_ in specs:
+        m = fem_inputs.box_mesh(s_["n"], s_["p"], perturb=0.1, seed=s_["mesh_seed"])
+        gm = fem.Mesh(m)
+        op = fem.Operator.bake_off(gm, "BP3", prec=fem.F32)
+        b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"],
+                                                    seed=s_["rhs_seed"])).cuda()
+        probs.append((gm, op, b))
+    batch = fem.Batch([q[1] for q in probs])
+    bs = [q[2] for q in probs]
+    t0 = time.perf_counter()
+    tune = batch.autotune(bs, [torch.zeros_like(b) for b in bs], iters=10)
+    t_tune = time.perf_counter() - t0
+    res = None
+    best = None
+    for _ in range(2):
+        xs = [torch.zeros_like(b) for b in bs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = batch.solve(bs, xs, rtol=1e-10, inner_rtol=1e-5)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        best = t if best is None else min(best, t)
+    worst = max(r["true_rel"] for r in res)
+    dof_it = sum(q[1].N * r["iterations"] for q, r in zip(probs, res))
+    seq = 0.0
+    for gm, op, b in probs:
+        x = torch.zeros_like(b)
+        op.solve_refined(b, x, rtol=1e-10, inner_rtol=1e-5)  # warm graphs
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op.solve_refined(b, x, rtol=1e-10, inner_rtol=1e-5)
+        torch.cuda.synchronize()
+        seq += time.perf_counter() - t0
+    return {"problems": len(probs), "total_dofs": sum(q[1].N for q in probs),
+            "orders": sorted(set(s_["p"] for s_ in specs)),
+            "seconds": best, "gdofs_per_cg_iteration": dof_it / best / 1e9,
+            "max_true_rel_residual": worst, "all_converged": all(r["status"] == "FEM_OK" for r in res),
+            "autotune": dict(tune, seconds=t_tune),
+            "sequential_refined_seconds": seq, "speedup_vs_sequential": seq / best}
+
+
+def section_learned(fem, torch, args):
+    """BP3 with kappa(x) = exp(Gaussian random field, l = 0.1, sigma = 1),
+    p=4, n^3 hexes: train the per-element network on Jacobi-PCG
+    residual/error pairs (GPU kernels), calibrate its weight, then time to a
+    1e-10 FP64 residual: plain FP64 Jacobi-PCG, FP32+FP64-refinement
+    Jacobi-PCG, and FP32 flexible CG with the learned preconditioner inside
+    FP64 refinement."""
+    p, n = 4, args.learned_n
+    rff = fem_inputs.rff_params(1024, 0.1, seed=77)
+    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=78)
+    gm = fem.Mesh(m)
+    t0 = time.perf_counter()
+    op = fem.Operator.bake_off(gm, "BP3", prec=fem.F32, rff=rff)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    P3 = (p + 1) ** 3
+    n_in, n_h, n_out = 160, 256, 128
+    net = fem.Mlp(n_in, n_h, n_out, fem_inputs.mlp_init(n_in, n_h, n_out, seed=79), mode=0)
+    pc = fem.Precond(op, net)
+    ks = (5, 20, 80)
+    nrhs = 2
+    E = m["E"]
+    X = torch.zeros(nrhs * len(ks) * E, n_in, dtype=torch.bfloat16, device="cuda")
+    T = torch.zeros(nrhs * len(ks) * E, n_out, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    r0 = 0
+    for j in range(nrhs):
+        b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=800 + j)).cuda()
+        xs = torch.zeros_like(b)
+        op.solve_refined(b, xs, rtol=1e-11, inner_rtol=1e-5)
+        for k in ks:
+            xk = torch.zeros_like(b)
+            op.cg(b, xk, maxit=k, rtol=0.0)
+            pc.samples(b, xs, xk, X[r0:r0 + E], T[r0:r0 + E])
+            r0 += E
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = net.train(X, T, P3, epochs=4, batch=4096, lr=1e-3, seed=1)
+    t_train = time.perf_counter() - t0
+    del X, T
+    bval = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=898)).cuda()
+    gamma = pc.calibrate(bval, probe_iters=64)
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=899)).cuda()
+    res = {}
+    for meth in ("fp64_jacobi_pcg", "fp32_refined_jacobi", "fp32_refined_learned_fcg",
+                 "fp32_refined_jacobi_fcg"):
+        best = None
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if meth == "fp64_jacobi_pcg":
+                st = op.cg(b, x, rtol=1e-10)
+            elif meth == "fp32_refined_jacobi":
+                st = op.solve_refined(b, x, rtol=1e-10, inner_rtol=1e-5)
+            elif meth == "fp32_refined_learned_fcg":
+                st = pc.fcg(b, x, rtol=1e-10)
+            else:
+                st = fem.Precond(op, None).fcg(b, x, rtol=1e-10)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            best = t if best is None else min(best, t)
+        r = op.residual(b, x)
+        res[meth] = {"seconds": best, "iterations": st["iterations"],
+                     "fallback": st.get("fallback", 0),
+                     "true_rel_residual": (torch.linalg.norm(r) / torch.linalg.norm(b)).item()}
+    return {"problem": "kappa BP3 p=%d n=%d N=%d" % (p, n, m["N"]), "setup_seconds": t_setup,
+            "training": {"samples": nrhs * len(ks) * E, "data_seconds": t_data,
+                         "train_seconds": t_train, "epochs": len(losses),
+                         "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
+                         "calibrated_gamma": gamma},
+            "time_to_1e-10": res,
+            "learned_vs_fp64_speedup": res["fp64_jacobi_pcg"]["seconds"] / res["fp32_refined_learned_fcg"]["seconds"],
+            "learned_vs_jacobi_fcg_iterations": res["fp32_refined_jacobi_fcg"]["iterations"] / max(1, res["fp32_refined_learned_fcg"]["iterations"])}
+
+
 def config(args, work):
     return {"workload": "BP3 FP64 Jacobi-PCG, Gauss-Legendre q=p+2, perturbed unit-cube "
                         "brick meshes of about %.0e DOFs per order" % args.dofs,
@@ -362,6 +572,13 @@ def main():
     del ops
     if args.tts_dofs > 0:
         line["time_to_solution"] = time_to_solution(fem, torch, args)
+    secs = [t for t in args.sections.split(",") if t]
+    if "bp56" in secs:
+        line["bp5_bp6"] = section_bp56(fem, torch, args)
+    if "batched" in secs:
+        line["batched"] = section_batched(fem, torch, args)
+    if "learned" in secs:
+        line["learned"] = section_learned(fem, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(work, args.iters, args.cpu_seconds)
     if rank == 0:

@@ -109,6 +109,17 @@ fem_status fem_mesh_create(int p, int64_t N, int64_t E,
                            const double *node_xyz_host,
                            const uint8_t *dirichlet_host, void *stream,
                            fem_mesh **out);
+/* Same as fem_mesh_create, with the node coordinates computed on the GPU
+ * from trilinear bricks (the map of fem_mesh_nodes_from_vertices):
+ * vert_xyz_host [nvert][3], elem_verts_host [E][8]. */
+fem_status fem_mesh_create_vertices(int p, int64_t N, int64_t E,
+                                    const int32_t *elem_nodes_host, int64_t nvert,
+                                    const double *vert_xyz_host,
+                                    const int32_t *elem_verts_host,
+                                    const uint8_t *dirichlet_host, void *stream,
+                                    fem_mesh **out);
+/* Node coordinates [N][3] of a mesh, copied to host (synchronizes). */
+fem_status fem_mesh_node_coords(const fem_mesh *mesh, double *xyz_host);
 fem_status fem_mesh_destroy(fem_mesh *mesh);
 
 /* ---------------------------------------------------------------- operator */

@@ -73,6 +73,9 @@ def lib():
         "fem_mesh_nodes_from_vertices": [ctypes.c_int, _I64, _I64, _VP, _VP, _VP, _I64, _VP],
         "fem_mesh_create": [ctypes.c_int, _I64, _I64, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)],
         "fem_mesh_destroy": [_VP],
+        "fem_mesh_create_vertices": [ctypes.c_int, _I64, _I64, _VP, _I64, _VP, _VP, _VP, _VP,
+                                     ctypes.POINTER(_VP)],
+        "fem_mesh_node_coords": [_VP, _VP],
         "fem_op_create": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                           ctypes.c_int, _VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_VP)],
         "fem_op_destroy": [_VP],
@@ -169,17 +172,33 @@ class Mesh:
 
     def __init__(self, mesh, node_xyz=None, stream=None):
         self.p = int(mesh["p"]); self.N = int(mesh["N"]); self.E = int(mesh["E"])
-        if node_xyz is None:
-            node_xyz = nodes_from_vertices(mesh)
-        self.node_xyz = np.ascontiguousarray(node_xyz, dtype=np.float64)
         en = np.ascontiguousarray(mesh["elem_nodes"], dtype=np.int32)
         dr = mesh.get("dirichlet")
         dr = None if dr is None else np.ascontiguousarray(dr, dtype=np.uint8)
         self.dirichlet = dr
         h = _VP()
-        _check(lib().fem_mesh_create(self.p, self.N, self.E, _ptr(en), _ptr(self.node_xyz),
-                                     _ptr(dr), _stream_handle(stream), ctypes.byref(h)))
+        if node_xyz is None:
+            # node coordinates computed on the GPU from the trilinear bricks
+            vx = np.ascontiguousarray(mesh["vert_xyz"], dtype=np.float64)
+            ev = np.ascontiguousarray(mesh["elem_verts"], dtype=np.int32)
+            _check(lib().fem_mesh_create_vertices(self.p, self.N, self.E, _ptr(en), vx.shape[0],
+                                                  _ptr(vx), _ptr(ev), _ptr(dr),
+                                                  _stream_handle(stream), ctypes.byref(h)))
+            self._xyz = None
+        else:
+            self._xyz = np.ascontiguousarray(node_xyz, dtype=np.float64)
+            _check(lib().fem_mesh_create(self.p, self.N, self.E, _ptr(en), _ptr(self._xyz),
+                                         _ptr(dr), _stream_handle(stream), ctypes.byref(h)))
         self._h = h
+
+    @property
+    def node_xyz(self):
+        """Node coordinates [N, 3] (copied from the device on first use)."""
+        if self._xyz is None:
+            xyz = np.zeros((self.N, 3))
+            _check(lib().fem_mesh_node_coords(self._h, _ptr(xyz)))
+            self._xyz = xyz
+        return self._xyz
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

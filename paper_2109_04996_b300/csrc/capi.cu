@@ -72,6 +72,110 @@ extern "C" fem_status fem_mesh_create(int p, int64_t N, int64_t E, const int32_t
   return FEM_OK;
 }
 
+namespace {
+// Q_p node coordinates of trilinear bricks on the GPU (same map as
+// fem_mesh_nodes_from_vertices): one thread per (element, local node).
+__global__ void nodes_from_vertices_kernel(int P, int64_t E, const double *z, const double *vxyz,
+                                           const int32_t *ev, const int32_t *en, int64_t N,
+                                           double *xyz) {
+  const int P3 = P * P * P;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E * P3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / P3;
+    const int l = (int)(i - e * P3);
+    const int a = l % P, b = (l / P) % P, c = l / (P * P);
+    const double h0[3] = {0.5 * (1.0 - z[a]), 0.5 * (1.0 - z[b]), 0.5 * (1.0 - z[c])};
+    const double h1[3] = {0.5 * (1.0 + z[a]), 0.5 * (1.0 + z[b]), 0.5 * (1.0 + z[c])};
+    double s[3] = {0, 0, 0};
+    for (int t = 0; t < 8; t++) {
+      const double f = ((t & 1) ? h1[0] : h0[0]) * ((t & 2) ? h1[1] : h0[1]) * ((t & 4) ? h1[2] : h0[2]);
+      const int64_t v = ev[8 * e + t];
+      for (int d = 0; d < 3; d++) s[d] += f * vxyz[3 * v + d];
+    }
+    const int64_t g = en[i];
+    for (int d = 0; d < 3; d++) xyz[d * N + g] = s[d];
+  }
+}
+}  // namespace
+
+extern "C" fem_status fem_mesh_create_vertices(int p, int64_t N, int64_t E, const int32_t *en,
+                                               int64_t nvert, const double *vxyz,
+                                               const int32_t *ev, const uint8_t *dir,
+                                               void *stream, fem_mesh **out) {
+  if (!out) { fem_set_error("fem_mesh_create_vertices: out is NULL"); return FEM_EINVAL; }
+  *out = nullptr;
+  if (p < 1 || p + 1 > FEM_MAX_P || N < 1 || E < 0 || nvert < 1 || (E > 0 && (!en || !ev)) || !vxyz) {
+    fem_set_error("fem_mesh_create_vertices: invalid arguments");
+    return FEM_EINVAL;
+  }
+  if (N > INT32_MAX || nvert > INT32_MAX) { fem_set_error("fem_mesh_create_vertices: sizes exceed int32 ids"); return FEM_EINVAL; }
+  const int P = p + 1, P3 = P * P * P;
+  for (int64_t i = 0; i < E * P3; i++)
+    if (en[i] < 0 || en[i] >= N) {
+      fem_set_error("fem_mesh_create_vertices: elem_nodes[%lld] = %d out of [0, %lld)", (long long)i, en[i], (long long)N);
+      return FEM_EINVAL;
+    }
+  for (int64_t i = 0; i < E * 8; i++)
+    if (ev[i] < 0 || ev[i] >= nvert) {
+      fem_set_error("fem_mesh_create_vertices: elem_verts[%lld] out of range", (long long)i);
+      return FEM_EINVAL;
+    }
+  BasisTables t;
+  fem_build_tables(p, p + 1, FEM_LOBATTO, &t);  // t.z: the Gauss-Lobatto nodes
+  fem_mesh *m = new fem_mesh();
+  m->p = p; m->P = P; m->N = N; m->E = E;
+  m->stream = (cudaStream_t)stream;
+  double *d_v = nullptr, *d_z = nullptr;
+  int32_t *d_ev = nullptr;
+  int rc;
+  if ((rc = dev_alloc(&m->d_elem_nodes, (size_t)E * P3, &m->bytes)) ||
+      (rc = dev_alloc(&m->d_xyz, (size_t)3 * N, &m->bytes)) ||
+      (rc = dev_alloc(&m->d_dirichlet, (size_t)N, &m->bytes))) {
+    fem_mesh_destroy(m);
+    return rc;
+  }
+  int64_t tmp = 0;
+  if ((rc = dev_alloc(&d_v, (size_t)3 * nvert, &tmp)) || (rc = dev_alloc(&d_ev, (size_t)8 * E, &tmp)) ||
+      (rc = dev_alloc(&d_z, (size_t)FEM_MAX_P, &tmp))) {
+    cudaFree(d_v); cudaFree(d_ev); cudaFree(d_z);
+    fem_mesh_destroy(m);
+    return rc;
+  }
+  cudaStream_t s = m->stream;
+  cudaError_t e = cudaMemcpyAsync(m->d_elem_nodes, en, sizeof(int32_t) * E * P3, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_v, vxyz, sizeof(double) * 3 * nvert, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && E > 0) e = cudaMemcpyAsync(d_ev, ev, sizeof(int32_t) * 8 * E, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_z, t.z, sizeof(double) * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (dir) e = cudaMemcpyAsync(m->d_dirichlet, dir, N, cudaMemcpyHostToDevice, s);
+    else e = cudaMemsetAsync(m->d_dirichlet, 0, N, s);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_xyz, 0, sizeof(double) * 3 * N, s);
+  if (e == cudaSuccess && E > 0) {
+    nodes_from_vertices_kernel<<<148 * 16, 256, 0, s>>>(P, E, d_z, d_v, d_ev, m->d_elem_nodes, N, m->d_xyz);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_v); cudaFree(d_ev); cudaFree(d_z);
+  if (e != cudaSuccess) {
+    fem_set_error("fem_mesh_create_vertices: %s", cudaGetErrorString(e));
+    fem_mesh_destroy(m);
+    return FEM_ECUDA;
+  }
+  *out = m;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_mesh_node_coords(const fem_mesh *m, double *xyz_host) {
+  if (!m || !xyz_host) { fem_set_error("fem_mesh_node_coords: invalid arguments"); return FEM_EINVAL; }
+  std::vector<double> soa((size_t)3 * m->N);
+  FEM_CUDA_TRY(cudaMemcpyAsync(soa.data(), m->d_xyz, sizeof(double) * 3 * m->N, cudaMemcpyDeviceToHost, m->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  for (int64_t i = 0; i < m->N; i++)
+    for (int d = 0; d < 3; d++) xyz_host[3 * i + d] = soa[(size_t)d * m->N + i];
+  return FEM_OK;
+}
+
 extern "C" fem_status fem_mesh_destroy(fem_mesh *m) {
   if (!m) return FEM_OK;
   cudaFree(m->d_elem_nodes); cudaFree(m->d_xyz); cudaFree(m->d_dirichlet);

@@ -1,18 +1,22 @@
 // Mixed-precision solve: FP64 iterative refinement around an FP32 inner
 // Jacobi-PCG.  The paper fixes the operator and the CG solve (sections
-// "Benchmarks" and "libCEED"); the refinement itself is classical iterative
-// refinement (Wilkinson; Carson & Higham 2018), applied to the same
-// Dirichlet-constrained system:
+// "Benchmarks" and "libCEED"); the refinement is classical iterative
+// refinement (Wilkinson; Carson & Higham 2018) with "reliable updates"
+// (Strzodka & Goeddeke 2006; Clark et al. 2010): the inner CG is not
+// restarted at each outer step, only its residual is replaced.
 //
 //   repeat:  r = b - A_64 x          (FP64 fused apply, FP64 vectors)
 //            stop if ||r|| <= rtol ||b||
-//            solve A_32 d = r        (FP32 apply, FP32 vectors, FP64 dot
-//                                     products and scalars) to inner_rtol
+//            r_32 = r, z = dinv r_32, p = z + beta p with
+//            beta = (r^T z) / (r^T z of the last inner iteration)
+//            (beta = 0 at the first step: p = z)
+//            continue the FP32 CG on A_32 d = r (FP32 apply, FP32 vectors,
+//            FP64 dot products and scalars) until ||r_32|| <= inner_rtol ||r||
 //            x = x + d               (FP64)
 //
-// Each outer step is one CUDA graph launch: residual kernel, a conditional
-// WHILE node over the inner CG body (apply, update, direction), correction
-// kernel.  The host reads one status word per outer step.
+// Each outer step is one CUDA graph launch: residual kernel, direction
+// kernel, a conditional WHILE node over the inner CG body (apply, update,
+// direction), correction kernel.  The host reads one status word per step.
 #include <math.h>
 
 #include "fem_internal.h"
@@ -76,18 +80,20 @@ __global__ void rf_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N
   }
 }
 
-// x <- M x, y64 <- 0 (before the first residual)
-__global__ void rf_prepare_kernel(double *x, double *y64, const uint8_t *dir, int64_t N,
+// x <- M x, y64 <- 0, p <- 0 (before the first residual)
+__global__ void rf_prepare_kernel(double *x, double *y64, float *p, const uint8_t *dir, int64_t N,
                                   int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (dir && dir[i % N]) x[i] = 0.0;
     y64[i] = 0.0;
+    p[i] = 0.0f;
   }
 }
 
-// Outer residual r64 = M (b - A x) (FP64), rounded to FP32 for the inner
-// solve, which starts from d = 0: r = r64, z = dinv r, p = z.
+// Outer residual r64 = M (b - A x) (FP64), rounded to FP32: the inner
+// solve's residual is replaced, r = r64, z = dinv r, d = 0; the direction
+// kernel that follows sets p = z + beta p (reliable update).
 __global__ void rf_residual_kernel(const RParams c) {
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
@@ -97,7 +103,7 @@ __global__ void rf_residual_kernel(const RParams c) {
     const double r64 = fixed ? 0.0 : bi - c.y64[i];
     const float r = (float)r64;
     const float z = c.dinv[i] * r;
-    c.r[i] = r; c.z[i] = z; c.p[i] = z; c.d[i] = 0.0f; c.y[i] = 0.0f;
+    c.r[i] = r; c.z[i] = z; c.d[i] = 0.0f; c.y[i] = 0.0f;
     c.y64[i] = 0.0;
     v[0] += r64 * r64; v[1] += bi * bi; v[2] += (double)r * (double)z; v[3] += (double)r * r;
   }
@@ -106,8 +112,11 @@ __global__ void rf_residual_kernel(const RParams c) {
     RefineScalars *s = c.sc;
     s->rr64 = tot[0]; s->bb64 = tot[1];
     CgScalars &in = s->in;
+    // beta of the reliable update: new r^T z over the last inner one (0 at
+    // the first step, where in.rz is 0 and p is 0)
+    in.beta = in.rz > 0.0 ? tot[2] / in.rz : 0.0;
     in.rz = tot[2]; in.rr = tot[3]; in.iter = 0; in.status = FEM_OK;
-    in.pAp = 0.0; in.alpha = 0.0; in.beta = 0.0;
+    in.pAp = 0.0; in.alpha = 0.0;
     const bool conv = !(tot[1] > 0.0) || tot[0] <= s->rtol2 * tot[1];
     const bool bad = !isfinite(tot[0]) || !isfinite(tot[2]);
     s->converged = conv ? 1 : 0;
@@ -245,6 +254,7 @@ int build_graph(fem_op *op, const double *b, double *x) {
     rc = fem_launch_apply_f64(op, x, w->y64, nullptr, op->E, nullptr);
     if (rc) break;
     rf_residual_kernel<<<g, kT, 0, w->cap>>>(c);
+    rf_direction_kernel<<<g, kT, 0, w->cap>>>(c);   // p = z + beta p
     e = cudaGetLastError();
     if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
     e = cudaStreamGetCaptureInfo(w->cap, &st, nullptr, &graph, &deps, nullptr, &ndeps);
@@ -321,7 +331,7 @@ extern "C" fem_status fem_solve_refined(fem_op *op, const double *b, double *x,
   init.inner_rtol2 = o->inner_rtol * o->inner_rtol;
   init.rtol2 = o->rtol * o->rtol;
   FEM_CUDA_TRY(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  rf_prepare_kernel<<<grid_for(w->n), kT, 0, s>>>(x, w->y64, op->mesh->d_dirichlet, op->N, w->n);
+  rf_prepare_kernel<<<grid_for(w->n), kT, 0, s>>>(x, w->y64, w->p, op->mesh->d_dirichlet, op->N, w->n);
   FEM_CHECK_LAUNCH();
   if (!w->exec || w->g_b != b || w->g_x != x) {
     FEM_CUDA_TRY(cudaStreamSynchronize(s));
