@@ -311,7 +311,7 @@ class Operator:
         return dict(epb_choice=r.epb_choice, blocks_per_sm=r.blocks_per_sm, us=r.us,
                     from_cache=bool(r.from_cache), candidates=r.candidates)
 
-    def solve_refined(self, b, x, rtol=1e-10, inner_rtol=1e-5, maxit=100000, max_outer=20,
+    def solve_refined(self, b, x, rtol=1e-10, inner_rtol=0.1, maxit=100000, max_outer=100,
                       precond=PC_JACOBI):
         """FP64 iterative refinement around an FP32 inner PCG (operator
         created with prec=F32).  x: initial guess in, solution out."""
@@ -349,7 +349,7 @@ class Batch:
         assert len(bs) == len(self.ops) == len(xs)
         return (_VP * len(bs))(*[_ptr(b) for b in bs]), (_VP * len(xs))(*[_ptr(x) for x in xs])
 
-    def solve(self, bs, xs, rtol=1e-10, inner_rtol=1e-5, maxit=100000, max_outer=20):
+    def solve(self, bs, xs, rtol=1e-10, inner_rtol=0.1, maxit=100000, max_outer=100):
         o = _CgOpts(PC_JACOBI, int(maxit), float(rtol), 0, float(inner_rtol), int(max_outer))
         st = (_CgStats * len(self.ops))()
         bv, xv = self._vecs(bs, xs)

@@ -62,10 +62,36 @@ struct ApplyShape {
   static constexpr int NT = ((Q2 * EPB + 31) / 32) * 32;
 };
 
+// FP32 diffusion stages each element group's pointwise data (6 q^3 values
+// per element) in shared memory with cp.async, issued when the group starts
+// so that its HBM latency hides behind the gather and the gradients.  (The
+// FP64 kernel is bound by the FP64 pipe and reads qdata directly.)
+template <typename T, int KIND>
+struct StageQ {
+  static constexpr bool value = sizeof(T) == 4 && KIND == FEM_DIFFUSION;
+};
+
+// shared-memory offset (in T) of the staged qdata: after the tables and the
+// cubes, rounded up to 16 bytes
+template <typename T, int Q, int P, int KIND, int EPB>
+constexpr size_t stage_offset() {
+  const size_t o = Q * P + Q * Q + (size_t)EPB * ((KIND == FEM_DIFFUSION) ? 3 : 2) * Q * Q * Q;
+  const size_t per16 = 16 / sizeof(T);
+  return (o + per16 - 1) / per16 * per16;
+}
+
 template <typename T, int Q, int P, int KIND, int EPB>
 constexpr size_t apply_smem_bytes() {
-  return sizeof(T) * (Q * P + Q * Q + (size_t)EPB * ((KIND == FEM_DIFFUSION) ? 3 : 2) * Q * Q * Q);
+  return sizeof(T) * (stage_offset<T, Q, P, KIND, EPB>() +
+                      (StageQ<T, KIND>::value ? (size_t)EPB * 6 * Q * Q * Q : 0));
 }
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename T>
 __device__ __forceinline__ void atomic_add(T *a, T v) { atomicAdd(a, v); }
@@ -76,6 +102,7 @@ struct Slab {
   int slot_raw, slot, tx, ty;
   bool live;
   T *sB, *sD, *su, *sv, *sw;
+  T *sq;   // staged qdata of the group [EPB][6][q^3] (FP32 diffusion)
   __device__ Slab(unsigned char *smem_raw) {
     constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
     constexpr int NCUBE = (KIND == FEM_DIFFUSION) ? 3 : 2;
@@ -90,6 +117,7 @@ struct Slab {
     su = cube + slot * NCUBE * Q3;
     sv = su + Q3;
     sw = (NCUBE == 3) ? sv + Q3 : sv;
+    sq = reinterpret_cast<T *>(smem_raw) + stage_offset<T, Q, P, KIND, EPB>();
   }
   __device__ void load_tables(const T *B, const T *Dq) {
     for (int i = threadIdx.x; i < Q * P; i += blockDim.x) sB[i] = B[i];
@@ -117,7 +145,21 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
   int64_t e = 0;
   if (valid) e = prm.list ? (int64_t)prm.list[k_el] : k_el;
   const int32_t *en = prm.elem_nodes + e * P3;
+  constexpr bool STAGE = StageQ<T, KIND>::value;
   const T *qd = prm.qdata + e * (int64_t)(ND * Q3) + (ty * Q + tx);
+  if constexpr (STAGE) {
+    // all threads copy the group's qdata (8-byte chunks: 6 q^3 is even)
+    for (int s_ = 0; s_ < EPB; s_++) {
+      const int64_t ks = g * EPB + s_;
+      if (ks >= prm.nsel) break;
+      const int64_t es = prm.list ? (int64_t)prm.list[ks] : ks;
+      const T *src = prm.qdata + es * (int64_t)(6 * Q3);
+      T *dst = sl.sq + s_ * 6 * Q3;
+      for (int ch = threadIdx.x; ch < 3 * Q3; ch += blockDim.x) cp_async8(dst + 2 * ch, src + 2 * ch);
+    }
+    cp_async_commit();
+    qd = sl.sq + sl.slot * 6 * Q3 + (ty * Q + tx);
+  }
     for (int c = 0; c < prm.ncomp; c++) {
       const T *xc = prm.x + c * N;
       T *yc = prm.y + c * N;
@@ -154,6 +196,9 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
             sz += sD[k * Q + m] * u[m];
           }
           gx[k] = sx; gy[k] = sy; gz[k] = sz;
+        }
+        if constexpr (STAGE) {
+          if (c == 0) { cp_async_wait_all(); __syncthreads(); }
         }
 #pragma unroll
         for (int k = 0; k < Q; k++) {
@@ -251,6 +296,9 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
               sz += sD[kq * Q + m] * tq[m];
             }
             gx[kq] = sx; gy[kq] = sy; gz[kq] = sz;
+          }
+          if constexpr (STAGE) {
+            if (c == 0) { cp_async_wait_all(); __syncthreads(); }
           }
 #pragma unroll
           for (int kq = 0; kq < Q; kq++) {

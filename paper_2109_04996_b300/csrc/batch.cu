@@ -57,8 +57,6 @@ struct BatchScalars {
   double rr64, bb64, rz0, rr0;   // residual-kernel accumulators
   double thresh;                  // inner threshold on ||r||^2
   double rr64_last, bb64_last;    // outer residual of the latest check
-  double rz_last;                 // r^T z at the end of the last inner solve
-  double beta_rep;                // reliable-update beta of this outer step
   int done_at;                    // iteration at which the inner solve ended
   int iter;                       // inner iterations of this outer step
   int total_iter, outer, converged, status;
@@ -283,10 +281,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         const bool ok = (pAp > 0.0) && isfinite(__ldcg(&s.rz[prev]) / pAp);
         if (ok) { s.iter += 1; s.total_iter += 1; }
         const double rzc = __ldcg(&s.rz[cur]), rrc = __ldcg(&s.rr[cur]);
-        if (!ok || !isfinite(rzc) || rrc <= s.thresh || s.iter >= a.maxit) {
-          s.done_at = k;
-          s.rz_last = ok ? rzc : __ldcg(&s.rz[prev]);
-        }
+        if (!ok || !isfinite(rzc) || rrc <= s.thresh || s.iter >= a.maxit) s.done_at = k;
       }
     }
     for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
@@ -337,6 +332,7 @@ __global__ void batch_residual_kernel(const BatchArgs a) {
       const double bj = fixed ? 0.0 : pr.b[j];
       const double r64 = fixed ? 0.0 : bj - pr.y64[j];
       const float r = (float)r64, z = pr.dinv[j] * r;
+      pr.p[j] += z - pr.z[j];  // reliable update: swap the residual part of p
       pr.r[j] = r; pr.z[j] = z; pr.d[j] = 0.0f; pr.y[j] = 0.0f;
       pr.y64[j] = 0.0;
       v[0] += r64 * r64; v[1] += bj * bj; v[2] += (double)r * z; v[3] += (double)r * r;
@@ -362,27 +358,11 @@ __global__ void batch_finalize_kernel(const BatchArgs a, double rtol2, double in
     else if (!(s.bb64 > 0.0) || s.rr64 <= rtol2 * s.bb64) s.converged = 1;
   }
   s.pAp[0] = s.pAp[1] = 0.0;
-  // reliable update: the inner CG continues with p = z + beta p
-  s.beta_rep = s.rz_last > 0.0 ? s.rz0 / s.rz_last : 0.0;
   s.rz[0] = 0.0; s.rz[1] = s.rz0;   // iteration 0 reads rz[1]
   s.rr[0] = s.rr[1] = 0.0;
   s.thresh = inner_rtol2 * s.rr0;
   s.iter = 0;
   s.done_at = s.converged ? -1 : INT_MAX;
-}
-
-// p = z + beta_rep p (p = z at the first step, where p = 0 and beta_rep = 0)
-__global__ void batch_direction_kernel(const BatchArgs a) {
-  const int64_t n_chunks = a.cstart[a.n];
-  for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
-    const int i = find_problem(a.cstart, a.n, it);
-    if (a.sc[i].converged) continue;
-    const BatchProblem &pr = a.prob[i];
-    const float beta = (float)a.sc[i].beta_rep;
-    const int64_t lo = (it - a.cstart[i]) * kChunk;
-    const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
-    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) pr.p[j] = pr.z[j] + beta * pr.p[j];
-  }
 }
 
 // x += d for problems still refining; clear the residual accumulators.
@@ -418,6 +398,7 @@ __global__ void batch_prepare_kernel(const BatchArgs a) {
       if (pr.dir && pr.dir[node]) pr.x[j] = 0.0;
       pr.y64[j] = 0.0;
       pr.p[j] = 0.0f;
+      pr.z[j] = 0.0f;
       pr.dinv[j] = (pr.dir && pr.dir[node]) ? 0.0f : (float)(1.0 / pr.diag[node]);
     }
   }
@@ -501,8 +482,6 @@ int run_solve(fem_batch *b, const fem_cg_opts *o, int *steps_out) {
     FEM_CHECK_LAUNCH();
     batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a, o->rtol * o->rtol,
                                                                      o->inner_rtol * o->inner_rtol);
-    FEM_CHECK_LAUNCH();
-    batch_direction_kernel<<<g, 256, 0, b->stream>>>(a);
     FEM_CHECK_LAUNCH();
     int rc = launch_inner(b, a, b->nt_choice, b->bps);
     if (rc) return rc;
@@ -734,7 +713,6 @@ extern "C" fem_status fem_batch_autotune(fem_batch *b, const double *const *bv,
       batch_apply64_kernel<<<b->ops[0]->nsm * 4, kNT64, batch_smem<double, kNT64>(), b->stream>>>(a, b->d_gstart64);
       batch_residual_kernel<<<b->ops[0]->nsm * 8, 256, 0, b->stream>>>(a);
       batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a, 0.0, 0.0);
-      batch_direction_kernel<<<b->ops[0]->nsm * 8, 256, 0, b->stream>>>(a);
       // keep every problem active for the timed iterations
       std::vector<BatchScalars> h(b->n);
       FEM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_sc, sizeof(BatchScalars) * b->n, cudaMemcpyDeviceToHost, b->stream));

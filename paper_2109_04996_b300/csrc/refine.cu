@@ -7,9 +7,10 @@
 //
 //   repeat:  r = b - A_64 x          (FP64 fused apply, FP64 vectors)
 //            stop if ||r|| <= rtol ||b||
-//            r_32 = r, z = dinv r_32, p = z + beta p with
-//            beta = (r^T z) / (r^T z of the last inner iteration)
-//            (beta = 0 at the first step: p = z)
+//            r_32 = r, z = dinv r_32 and p += z - z_old: the direction
+//            keeps its history (the last inner step formed p = z_old +
+//            beta p_prev; its residual part is swapped for the true one;
+//            p = z at the first step, where p = z_old = 0)
 //            continue the FP32 CG on A_32 d = r (FP32 apply, FP32 vectors,
 //            FP64 dot products and scalars) until ||r_32|| <= inner_rtol ||r||
 //            x = x + d               (FP64)
@@ -80,20 +81,21 @@ __global__ void rf_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N
   }
 }
 
-// x <- M x, y64 <- 0, p <- 0 (before the first residual)
-__global__ void rf_prepare_kernel(double *x, double *y64, float *p, const uint8_t *dir, int64_t N,
-                                  int64_t n) {
+// x <- M x, y64 <- 0, p <- 0, z <- 0 (before the first residual)
+__global__ void rf_prepare_kernel(double *x, double *y64, float *p, float *z, const uint8_t *dir,
+                                  int64_t N, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (dir && dir[i % N]) x[i] = 0.0;
     y64[i] = 0.0;
     p[i] = 0.0f;
+    z[i] = 0.0f;
   }
 }
 
 // Outer residual r64 = M (b - A x) (FP64), rounded to FP32: the inner
-// solve's residual is replaced, r = r64, z = dinv r, d = 0; the direction
-// kernel that follows sets p = z + beta p (reliable update).
+// solve's residual is replaced, r = r64, z = dinv r, d = 0, and the
+// direction's residual part is swapped, p += z - z_old (reliable update).
 __global__ void rf_residual_kernel(const RParams c) {
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
@@ -103,6 +105,7 @@ __global__ void rf_residual_kernel(const RParams c) {
     const double r64 = fixed ? 0.0 : bi - c.y64[i];
     const float r = (float)r64;
     const float z = c.dinv[i] * r;
+    c.p[i] += z - c.z[i];
     c.r[i] = r; c.z[i] = z; c.d[i] = 0.0f; c.y[i] = 0.0f;
     c.y64[i] = 0.0;
     v[0] += r64 * r64; v[1] += bi * bi; v[2] += (double)r * (double)z; v[3] += (double)r * r;
@@ -112,9 +115,7 @@ __global__ void rf_residual_kernel(const RParams c) {
     RefineScalars *s = c.sc;
     s->rr64 = tot[0]; s->bb64 = tot[1];
     CgScalars &in = s->in;
-    // beta of the reliable update: new r^T z over the last inner one (0 at
-    // the first step, where in.rz is 0 and p is 0)
-    in.beta = in.rz > 0.0 ? tot[2] / in.rz : 0.0;
+    in.beta = 0.0;
     in.rz = tot[2]; in.rr = tot[3]; in.iter = 0; in.status = FEM_OK;
     in.pAp = 0.0; in.alpha = 0.0;
     const bool conv = !(tot[1] > 0.0) || tot[0] <= s->rtol2 * tot[1];
@@ -254,7 +255,6 @@ int build_graph(fem_op *op, const double *b, double *x) {
     rc = fem_launch_apply_f64(op, x, w->y64, nullptr, op->E, nullptr);
     if (rc) break;
     rf_residual_kernel<<<g, kT, 0, w->cap>>>(c);
-    rf_direction_kernel<<<g, kT, 0, w->cap>>>(c);   // p = z + beta p
     e = cudaGetLastError();
     if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
     e = cudaStreamGetCaptureInfo(w->cap, &st, nullptr, &graph, &deps, nullptr, &ndeps);
@@ -331,7 +331,8 @@ extern "C" fem_status fem_solve_refined(fem_op *op, const double *b, double *x,
   init.inner_rtol2 = o->inner_rtol * o->inner_rtol;
   init.rtol2 = o->rtol * o->rtol;
   FEM_CUDA_TRY(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
-  rf_prepare_kernel<<<grid_for(w->n), kT, 0, s>>>(x, w->y64, w->p, op->mesh->d_dirichlet, op->N, w->n);
+  rf_prepare_kernel<<<grid_for(w->n), kT, 0, s>>>(x, w->y64, w->p, w->z, op->mesh->d_dirichlet,
+                                                   op->N, w->n);
   FEM_CHECK_LAUNCH();
   if (!w->exec || w->g_b != b || w->g_x != x) {
     FEM_CUDA_TRY(cudaStreamSynchronize(s));
