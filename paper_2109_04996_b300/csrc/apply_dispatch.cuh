@@ -19,7 +19,7 @@ struct EpbChoice {
 template <typename T, int P, int Q, int KIND, bool COLLOC, int EPB>
 int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
-  constexpr size_t smem = apply_smem_bytes<T, Q, P, KIND, EPB>();
+  constexpr size_t smem = apply_smem_bytes<T, Q, P, KIND, EPB, COLLOC>();
   if constexpr (NT > 1024 || smem > 200 * 1024) {
     fem_set_error("apply: launch shape EPB=%d not valid for P=%d q=%d", EPB, P, Q);
     return FEM_EINVAL;
@@ -46,6 +46,7 @@ int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
 
 template <typename T, int P, int Q, int KIND, bool COLLOC>
 int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
+
   switch (choice) {
     case 1: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 1>::value>(op, prm, bps);
     case 2: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);

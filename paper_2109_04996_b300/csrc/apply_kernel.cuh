@@ -62,13 +62,15 @@ struct ApplyShape {
   static constexpr int NT = ((Q2 * EPB + 31) / 32) * 32;
 };
 
-// FP32 diffusion stages each element group's pointwise data (6 q^3 values
-// per element) in shared memory with cp.async, issued when the group starts
-// so that its HBM latency hides behind the gather and the gradients.  (The
-// FP64 kernel is bound by the FP64 pipe and reads qdata directly.)
-template <typename T, int KIND>
+// The collocated FP32 diffusion kernel (BP5/BP6) stages each element group's
+// pointwise data (6 q^3 values per element) in shared memory with cp.async,
+// issued when the group starts so that its HBM latency hides behind the
+// gather and the gradients.  (Measured: faster for the collocated kernel,
+// slower for the Gauss-Legendre one, whose shared-memory traffic is higher;
+// the FP64 kernels are bound by the FP64 pipe and read qdata directly.)
+template <typename T, int KIND, bool COLLOC = true>
 struct StageQ {
-  static constexpr bool value = sizeof(T) == 4 && KIND == FEM_DIFFUSION;
+  static constexpr bool value = sizeof(T) == 4 && KIND == FEM_DIFFUSION && COLLOC;
 };
 
 // shared-memory offset (in T) of the staged qdata: after the tables and the
@@ -80,10 +82,19 @@ constexpr size_t stage_offset() {
   return (o + per16 - 1) / per16 * per16;
 }
 
-template <typename T, int Q, int P, int KIND, int EPB>
+template <typename T, int Q, int P, int KIND, int EPB, bool COLLOC = false>
 constexpr size_t apply_smem_bytes() {
   return sizeof(T) * (stage_offset<T, Q, P, KIND, EPB>() +
-                      (StageQ<T, KIND>::value ? (size_t)EPB * 6 * Q * Q * Q : 0));
+                      (StageQ<T, KIND, COLLOC>::value ? (size_t)EPB * 6 * Q * Q * Q : 0));
+}
+
+// Row `row` of a shared table with `stride` between entries, into registers.
+// (Loaded once per stage: the compiler cannot hoist these loads out of the
+// stage loops itself because the loops also store to shared memory.)
+template <int N, typename T>
+__device__ __forceinline__ void load_row(const T *base, int stride, T (&out)[N]) {
+#pragma unroll
+  for (int m = 0; m < N; m++) out[m] = base[m * stride];
 }
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
@@ -145,7 +156,7 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
   int64_t e = 0;
   if (valid) e = prm.list ? (int64_t)prm.list[k_el] : k_el;
   const int32_t *en = prm.elem_nodes + e * P3;
-  constexpr bool STAGE = StageQ<T, KIND>::value;
+  constexpr bool STAGE = StageQ<T, KIND, COLLOC>::value;
   const T *qd = prm.qdata + e * (int64_t)(ND * Q3) + (ty * Q + tx);
   if constexpr (STAGE) {
     // all threads copy the group's qdata (8-byte chunks: 6 q^3 is even)
@@ -186,16 +197,21 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
         }
         __syncthreads();
         T gx[Q], gy[Q], gz[Q];
+        {
+          T dX[Q], dY[Q];
+          load_row<Q>(sD + tx * Q, 1, dX);
+          load_row<Q>(sD + ty * Q, 1, dY);
 #pragma unroll
-        for (int k = 0; k < Q; k++) {
-          T sx = 0, sy = 0, sz = 0;
+          for (int k = 0; k < Q; k++) {
+            T sx = 0, sy = 0, sz = 0;
 #pragma unroll
-          for (int m = 0; m < Q; m++) {
-            sx += sD[tx * Q + m] * su[(k * Q + ty) * Q + m];
-            sy += sD[ty * Q + m] * su[(k * Q + m) * Q + tx];
-            sz += sD[k * Q + m] * u[m];
+            for (int m = 0; m < Q; m++) {
+              sx += dX[m] * su[(k * Q + ty) * Q + m];
+              sy += dY[m] * su[(k * Q + m) * Q + tx];
+              sz += sD[k * Q + m] * u[m];
+            }
+            gx[k] = sx; gy[k] = sy; gz[k] = sz;
           }
-          gx[k] = sx; gy[k] = sy; gz[k] = sz;
         }
         if constexpr (STAGE) {
           if (c == 0) { cp_async_wait_all(); __syncthreads(); }
@@ -218,13 +234,16 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
           gz[k] = vz;
         }
         __syncthreads();
+        T dXT[Q], dYT[Q];
+        load_row<Q>(sD + tx, Q, dXT);
+        load_row<Q>(sD + ty, Q, dYT);
 #pragma unroll
         for (int k = 0; k < Q; k++) {
           T s = 0;
 #pragma unroll
           for (int m = 0; m < Q; m++) {
-            s += sD[m * Q + tx] * sv[(k * Q + ty) * Q + m];
-            s += sD[m * Q + ty] * sw[(k * Q + m) * Q + tx];
+            s += dXT[m] * sv[(k * Q + ty) * Q + m];
+            s += dYT[m] * sw[(k * Q + m) * Q + tx];
             s += sD[m * Q + k] * gz[m];
           }
           if (valid) {
@@ -255,22 +274,28 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
         __syncthreads();
         // B along y: thread (i < P, jq)
         if (tx < P && live) {
+          T bY[P];
+          load_row<P>(sB + ty * P, 1, bY);
 #pragma unroll
           for (int kq = 0; kq < Q; kq++) {
             T s = 0;
 #pragma unroll
-            for (int j = 0; j < P; j++) s += sB[ty * P + j] * su[(kq * Q + j) * Q + tx];
+            for (int j = 0; j < P; j++) s += bY[j] * su[(kq * Q + j) * Q + tx];
             sv[(kq * Q + ty) * Q + tx] = s;
           }
         }
         __syncthreads();
         // B along x: thread (iq, jq) -> values at its column of quadrature points
+        {
+          T bX[P];
+          load_row<P>(sB + tx * P, 1, bX);
 #pragma unroll
-        for (int kq = 0; kq < Q; kq++) {
-          T s = 0;
+          for (int kq = 0; kq < Q; kq++) {
+            T s = 0;
 #pragma unroll
-          for (int i = 0; i < P; i++) s += sB[tx * P + i] * sv[(kq * Q + ty) * Q + i];
-          tq[kq] = s;
+            for (int i = 0; i < P; i++) s += bX[i] * sv[(kq * Q + ty) * Q + i];
+            tq[kq] = s;
+          }
         }
         if constexpr (KIND == FEM_MASS) {
 #pragma unroll
@@ -286,16 +311,21 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
           }
           __syncthreads();
           T gx[Q], gy[Q], gz[Q];
+          {
+            T dX[Q], dY[Q];
+            load_row<Q>(sD + tx * Q, 1, dX);
+            load_row<Q>(sD + ty * Q, 1, dY);
 #pragma unroll
-          for (int kq = 0; kq < Q; kq++) {
-            T sx = 0, sy = 0, sz = 0;
+            for (int kq = 0; kq < Q; kq++) {
+              T sx = 0, sy = 0, sz = 0;
 #pragma unroll
-            for (int m = 0; m < Q; m++) {
-              sx += sD[tx * Q + m] * su[(kq * Q + ty) * Q + m];
-              sy += sD[ty * Q + m] * su[(kq * Q + m) * Q + tx];
-              sz += sD[kq * Q + m] * tq[m];
+              for (int m = 0; m < Q; m++) {
+                sx += dX[m] * su[(kq * Q + ty) * Q + m];
+                sy += dY[m] * su[(kq * Q + m) * Q + tx];
+                sz += sD[kq * Q + m] * tq[m];
+              }
+              gx[kq] = sx; gy[kq] = sy; gz[kq] = sz;
             }
-            gx[kq] = sx; gy[kq] = sy; gz[kq] = sz;
           }
           if constexpr (STAGE) {
             if (c == 0) { cp_async_wait_all(); __syncthreads(); }
@@ -319,16 +349,21 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
           }
           __syncthreads();
           // transposed gradient, back on the quadrature points
+          {
+            T dXT[Q], dYT[Q];
+            load_row<Q>(sD + tx, Q, dXT);
+            load_row<Q>(sD + ty, Q, dYT);
 #pragma unroll
-          for (int kq = 0; kq < Q; kq++) {
-            T s = 0;
+            for (int kq = 0; kq < Q; kq++) {
+              T s = 0;
 #pragma unroll
-            for (int m = 0; m < Q; m++) {
-              s += sD[m * Q + tx] * sv[(kq * Q + ty) * Q + m];
-              s += sD[m * Q + ty] * sw[(kq * Q + m) * Q + tx];
-              s += sD[m * Q + kq] * gz[m];
+              for (int m = 0; m < Q; m++) {
+                s += dXT[m] * sv[(kq * Q + ty) * Q + m];
+                s += dYT[m] * sw[(kq * Q + m) * Q + tx];
+                s += sD[m * Q + kq] * gz[m];
+              }
+              tq[kq] = s;
             }
-            tq[kq] = s;
           }
           if (live) {
 #pragma unroll
@@ -338,23 +373,29 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
         }
         // B^T along x: thread (i < P, jq)
         if (tx < P && live) {
+          T bXT[Q];
+          load_row<Q>(sB + tx, P, bXT);
 #pragma unroll
           for (int kq = 0; kq < Q; kq++) {
             T s = 0;
 #pragma unroll
-            for (int m = 0; m < Q; m++) s += sB[m * P + tx] * su[(kq * Q + ty) * Q + m];
+            for (int m = 0; m < Q; m++) s += bXT[m] * su[(kq * Q + ty) * Q + m];
             sv[(kq * Q + ty) * Q + tx] = s;
           }
         }
         __syncthreads();
         if (own) {
           // B^T along y: thread (i, j)
+          {
+            T bYT[Q];
+            load_row<Q>(sB + ty, P, bYT);
 #pragma unroll
-          for (int kq = 0; kq < Q; kq++) {
-            T s = 0;
+            for (int kq = 0; kq < Q; kq++) {
+              T s = 0;
 #pragma unroll
-            for (int m = 0; m < Q; m++) s += sB[m * P + ty] * sv[(kq * Q + m) * Q + tx];
-            tq[kq] = s;
+              for (int m = 0; m < Q; m++) s += bYT[m] * sv[(kq * Q + m) * Q + tx];
+              tq[kq] = s;
+            }
           }
           // B^T along z (registers) and scatter-add
 #pragma unroll

@@ -99,7 +99,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid barrier with a wall-clock limit.  Returns false (every block) once
-// any block has recorded an error.  extra: arrivals that never come (a test
+// any block has recorded an error.  Memory written before the barrier by any
+// block is visible to ordinary loads after it: thread 0 fences (fence.sc at
+// GPU scope) before arriving and after seeing the release, and the block's
+// bar.sync orders its other threads after thread 0.  extra: arrivals that never come (a test
 // hook that makes the wait run out); 0 in normal use.
 __device__ bool grid_barrier(BatchSync *s, unsigned extra, unsigned long long timeout_ns) {
   __syncthreads();
@@ -161,7 +164,7 @@ struct BatchEpb {
 // One element group of problem `pr` in precision T (FP32 inner / FP64 outer).
 template <typename T, int NT, int P>
 __device__ void batch_group(const BatchProblem &pr, int64_t g, const T *x, T *y,
-                            unsigned char *smem, double &dot) {
+                            unsigned char *smem, double &dot, bool reload) {
   constexpr int Q = P + 1;
   constexpr int EPB = BatchEpb<NT, Q>::value;
   ApplyParams<T> prm;
@@ -170,26 +173,31 @@ __device__ void batch_group(const BatchProblem &pr, int64_t g, const T *x, T *y,
   if constexpr (sizeof(T) == 4) { prm.qdata = (const T *)pr.qdata32; prm.B = (const T *)pr.B32; prm.Dq = (const T *)pr.Dq32; }
   else { prm.qdata = (const T *)pr.qdata64; prm.B = (const T *)pr.B64; prm.Dq = (const T *)pr.Dq64; }
   prm.partials = nullptr; prm.counter = nullptr; prm.dot_out = nullptr;
-  prm.x_l2_only = 1;  // x (the direction p) was written by other blocks
+  // x (the direction p) was written by other blocks before the last grid
+  // barrier, whose fence.sc / bar.sync pair orders it before these loads
+  // (the pattern of a cooperative grid sync): ordinary loads see it
+  prm.x_l2_only = 0;
   Slab<T, P, Q, FEM_DIFFUSION, EPB> sl(smem);
-  __syncthreads();  // previous item may still read the tables
-  sl.load_tables(prm.B, prm.Dq);
-  __syncthreads();
+  if (reload) {  // a new problem: its tables (the previous item may still read the old ones)
+    __syncthreads();
+    sl.load_tables(prm.B, prm.Dq);
+    __syncthreads();
+  }
   apply_group<T, P, Q, FEM_DIFFUSION, false, EPB>(prm, g, sl, dot);
 }
 
 template <typename T, int NT>
 __device__ void batch_group_p(const BatchProblem &pr, int64_t g, const T *x, T *y,
-                              unsigned char *smem, double &dot) {
+                              unsigned char *smem, double &dot, bool reload) {
   switch (pr.P) {
-    case 2: batch_group<T, NT, 2>(pr, g, x, y, smem, dot); break;
-    case 3: batch_group<T, NT, 3>(pr, g, x, y, smem, dot); break;
-    case 4: batch_group<T, NT, 4>(pr, g, x, y, smem, dot); break;
-    case 5: batch_group<T, NT, 5>(pr, g, x, y, smem, dot); break;
-    case 6: batch_group<T, NT, 6>(pr, g, x, y, smem, dot); break;
-    case 7: batch_group<T, NT, 7>(pr, g, x, y, smem, dot); break;
-    case 8: batch_group<T, NT, 8>(pr, g, x, y, smem, dot); break;
-    case 9: batch_group<T, NT, 9>(pr, g, x, y, smem, dot); break;
+    case 2: batch_group<T, NT, 2>(pr, g, x, y, smem, dot, reload); break;
+    case 3: batch_group<T, NT, 3>(pr, g, x, y, smem, dot, reload); break;
+    case 4: batch_group<T, NT, 4>(pr, g, x, y, smem, dot, reload); break;
+    case 5: batch_group<T, NT, 5>(pr, g, x, y, smem, dot, reload); break;
+    case 6: batch_group<T, NT, 6>(pr, g, x, y, smem, dot, reload); break;
+    case 7: batch_group<T, NT, 7>(pr, g, x, y, smem, dot, reload); break;
+    case 8: batch_group<T, NT, 8>(pr, g, x, y, smem, dot, reload); break;
+    case 9: batch_group<T, NT, 9>(pr, g, x, y, smem, dot, reload); break;
   }
 }
 
@@ -230,14 +238,27 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         a.sc[i].rr[cur] = 0.0;
       }
     }
+    // a block's items of one problem are consecutive in its stride: tables
+    // are loaded and p^T A p is flushed once per problem, not per item
+    int cur_prob = -1;
+    double dot = 0.0;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
       const int i = find_problem(a.gstart, a.n, it);
       if (__ldcg(&a.sc[i].done_at) < k) continue;   // uniform per block
+      if (i != cur_prob) {
+        if (cur_prob >= 0) {
+          const double s = block_sum(dot, red);
+          if (threadIdx.x == 0) atomicAdd(&a.sc[cur_prob].pAp[cur], s);
+        }
+        dot = 0.0;
+      }
       const BatchProblem &pr = a.prob[i];
-      double dot = 0.0;
-      batch_group_p<float, NT>(pr, it - a.gstart[i], pr.p, pr.y, smem, dot);
+      batch_group_p<float, NT>(pr, it - a.gstart[i], pr.p, pr.y, smem, dot, i != cur_prob);
+      cur_prob = i;
+    }
+    if (cur_prob >= 0) {
       const double s = block_sum(dot, red);
-      if (threadIdx.x == 0) atomicAdd(&a.sc[i].pAp[cur], s);
+      if (threadIdx.x == 0) atomicAdd(&a.sc[cur_prob].pAp[cur], s);
     }
     if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
     // -------- update phase
@@ -256,7 +277,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         const bool fixed = pr.dir && pr.dir[j % pr.N];
         float r = pr.r[j];
         pr.d[j] += af * pr.p[j];
-        if (!fixed) r -= af * __ldcg(&pr.y[j]);  // y: atomics of other blocks
+        if (!fixed) r -= af * pr.y[j];  // atomics of other blocks, before the barrier
         pr.r[j] = r;
         const float z = pr.dinv[j] * r;
         pr.z[j] = z;
@@ -307,12 +328,14 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
 __global__ void __launch_bounds__(kNT64) batch_apply64_kernel(const BatchArgs a, const int64_t *gstart64) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t n_items = gstart64[a.n];
+  int cur_prob = -1;
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int i = find_problem(gstart64, a.n, it);
     if (a.sc[i].converged) continue;
     const BatchProblem &pr = a.prob[i];
     double dot = 0.0;
-    batch_group_p<double, kNT64>(pr, it - gstart64[i], pr.x, pr.y64, smem, dot);
+    batch_group_p<double, kNT64>(pr, it - gstart64[i], pr.x, pr.y64, smem, dot, i != cur_prob);
+    cur_prob = i;
   }
 }
 
