@@ -180,10 +180,13 @@ fem_status fem_op_rhs(fem_op *op, int which, double *b);
 
 /* ---------------------------------------------------------------- autotuning */
 
-/* Launch shape of the fused apply: elements per block (a choice index:
- * 0 = about 256 threads per block, 1 = half that, 2 = twice that; only
- * diffusion operators with q = p+2 Gauss or collocated Lobatto have choices
- * 1 and 2) and resident blocks per SM (0 = the occupancy maximum). */
+/* Launch shape of the fused apply.  epb_choice selects the element body and
+ * the elements per block: for diffusion 0, 1, 2 = the line-based body with
+ * even-odd split 1D operators and about 256, 128 or 512 threads per block,
+ * 3, 4, 5 = the slab body (one thread per quadrature column) with the same
+ * three sizes; for mass 0, 1, 2 = the slab body (only 0 when collocated).
+ * blocks_per_sm: resident blocks per SM (0 = the occupancy maximum).
+ * Defaults: diffusion FP32 0; FP64 0 for Gauss with q >= 8, else 3. */
 typedef struct {
   int epb_choice;
   int blocks_per_sm;

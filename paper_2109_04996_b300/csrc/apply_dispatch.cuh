@@ -3,7 +3,7 @@
 // autotuner picks.  Included once per arithmetic type (apply_f64.cu,
 // apply_f32.cu).
 #pragma once
-#include "apply_kernel.cuh"
+#include "apply_lines.cuh"
 
 namespace fem_apply {
 
@@ -44,9 +44,60 @@ int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
   }
 }
 
+// Diffusion: the line-based, even-odd element body (apply_lines.cuh).
+template <typename T, int P, int Q, bool COLLOC, int EPB>
+int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
+  constexpr int NT = ApplyShape<Q, EPB>::NT;
+  constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
+  if constexpr (NT > 1024 || smem > 200 * 1024) {
+    fem_set_error("apply: launch shape EPB=%d not valid for P=%d q=%d", EPB, P, Q);
+    return FEM_EINVAL;
+  } else {
+    LineParams<T, P, Q> lp;
+    lp.a = prm;
+    double Bt[FEM_MAX_P * FEM_MAX_Q], Dt[FEM_MAX_Q * FEM_MAX_Q];
+    for (int k = 0; k < Q; k++)
+      for (int a = 0; a < P; a++) Bt[a * Q + k] = op->tab.B[k * P + a];
+    for (int k = 0; k < Q; k++)
+      for (int m = 0; m < Q; m++) Dt[m * Q + k] = op->tab.Dq[k * Q + m];
+    make_symtab<T, P, Q>(op->tab.B, lp.t.Bf);
+    make_symtab<T, Q, P>(Bt, lp.t.Bt);
+    make_symtab<T, Q, Q>(op->tab.Dq, lp.t.Df);
+    make_symtab<T, Q, Q>(Dt, lp.t.Dt);
+    auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB>;
+    static int max_bps = -1;
+    if (max_bps < 0) {
+      FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+      max_bps = per_sm < 1 ? 1 : per_sm;
+    }
+    const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
+    const int64_t ngroups = (prm.nsel + EPB - 1) / EPB;
+    int64_t grid = (int64_t)op->nsm * use;
+    if (grid > ngroups) grid = ngroups;
+    if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, NT, smem, op->stream()>>>(lp);
+    FEM_CHECK_LAUNCH();
+    return FEM_OK;
+  }
+}
+
+// Launch shape choice: 0..2 the line-based body with the three EPB
+// candidates, 3..5 the slab body (diffusion); mass has only the slab body.
 template <typename T, int P, int Q, int KIND, bool COLLOC>
 int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
-
+  if constexpr (KIND == FEM_DIFFUSION) {
+    switch (choice) {
+      case 0: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 0>::value>(op, prm, bps);
+      case 1: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 1>::value>(op, prm, bps);
+      case 2: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);
+      case 4: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 1>::value>(op, prm, bps);
+      case 5: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);
+      default: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 0>::value>(op, prm, bps);
+    }
+  }
   switch (choice) {
     case 1: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 1>::value>(op, prm, bps);
     case 2: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);
@@ -63,7 +114,7 @@ int dispatch_q(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
     if (op->colloc)
       return diff ? launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps)
                   : launch_shape<T, P, P, FEM_MASS, true, EpbChoice<P, 0>::value>(op, prm, bps);
-    return diff ? launch_shape<T, P, P, FEM_DIFFUSION, false, EpbChoice<P, 0>::value>(op, prm, bps)
+    return diff ? launch_epb<T, P, P, FEM_DIFFUSION, false>(op, prm, choice, bps)
                 : launch_shape<T, P, P, FEM_MASS, false, EpbChoice<P, 0>::value>(op, prm, bps);
   }
   if (op->Q == P + 1 && QG == P + 1)
@@ -89,9 +140,9 @@ int dispatch(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
   return FEM_EINVAL;
 }
 
-// Number of valid EPB choices for this operator (1 if not tunable).
+// Number of launch shape choices for this operator.
 inline int epb_choices(const fem_op *op) {
-  return op->kind == FEM_DIFFUSION && (op->colloc || op->Q == op->P + 1) ? 3 : 1;
+  return op->kind == FEM_DIFFUSION ? 6 : (op->colloc ? 1 : 3);
 }
 
 }  // namespace fem_apply

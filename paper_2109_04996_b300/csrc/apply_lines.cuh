@@ -1,0 +1,320 @@
+// Line-based element body of the fused diffusion apply, with even-odd
+// split 1D operators.
+//
+// The 1D tables are symmetric under reversal of both indices because the
+// Gauss and Gauss-Lobatto points are symmetric about 0:
+//   interpolation  B[q-1-k][P-1-a] =  B[k][a]
+//   derivative     D[q-1-k][q-1-m] = -D[k][m]
+// so a 1D contraction out = M in over a whole line splits into its even and
+// odd parts (Solomonoff, J. Comput. Phys. 98, 1992): with
+//   ie[a] = in[a] + in[NI-1-a],  io[a] = in[a] - in[NI-1-a]   (a < NI/2)
+// every pair (out[k], out[NO-1-k]) costs about NI FMAs instead of 2 NI.
+// That saving needs one thread to own a whole line, so here every stage
+// assigns lines to threads (rotating the axis from stage to stage) and the
+// stages exchange their results through shared-memory cubes:
+//   z-interp (registers) -> y-interp -> x-interp -> x/y/z derivatives ->
+//   pointwise D -> transposed derivatives (in place) -> transposed x, y, z
+//   interpolation -> scatter.
+// Collocated Gauss-Lobatto (BP5/BP6) skips the interpolation stages.  The
+// split tables are kernel parameters: every lane reads the same entry, which
+// the constant bank broadcasts.
+#pragma once
+#include "apply_kernel.cuh"
+
+namespace fem_apply {
+
+// Split table of an NI -> NO contraction M[NO][NI] with reversal symmetry S.
+template <typename T, int NI, int NO>
+struct SymTab {
+  static constexpr int HI = NI / 2, HO = NO / 2;
+  T e[HO + 1][HI > 0 ? HI : 1];  // (M[k][a] + M[k][NI-1-a]) / 2
+  T o[HO + 1][HI > 0 ? HI : 1];  // (M[k][a] - M[k][NI-1-a]) / 2
+  T mid[HO + 1];                 // M[k][NI/2] (NI odd)
+};
+
+// out = M in over one line.  S = +1: M[NO-1-k][NI-1-a] = M[k][a];
+// S = -1: M[NO-1-k][NI-1-a] = -M[k][a].
+template <int S, typename T, int NI, int NO>
+__device__ __forceinline__ void sym_apply(const SymTab<T, NI, NO> &M, const T (&in)[NI],
+                                          T (&out)[NO]) {
+  constexpr int HI = NI / 2, HO = NO / 2;
+  T ie[HI > 0 ? HI : 1], io[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int a = 0; a < HI; a++) {
+    ie[a] = in[a] + in[NI - 1 - a];
+    io[a] = in[a] - in[NI - 1 - a];
+  }
+#pragma unroll
+  for (int k = 0; k < HO; k++) {
+    T A = 0, Bv = 0;
+#pragma unroll
+    for (int a = 0; a < HI; a++) {
+      A += M.e[k][a] * ie[a];
+      Bv += M.o[k][a] * io[a];
+    }
+    if constexpr (NI % 2 == 1) A += M.mid[k] * in[HI];
+    out[k] = A + Bv;
+    out[NO - 1 - k] = (S > 0) ? A - Bv : Bv - A;
+  }
+  if constexpr (NO % 2 == 1) {
+    T v = 0;
+    if constexpr (S > 0) {
+#pragma unroll
+      for (int a = 0; a < HI; a++) v += M.e[HO][a] * ie[a];
+      if constexpr (NI % 2 == 1) v += M.mid[HO] * in[HI];
+    } else {
+#pragma unroll
+      for (int a = 0; a < HI; a++) v += M.o[HO][a] * io[a];
+    }
+    out[HO] = v;
+  }
+}
+
+template <typename T, int P, int Q>
+struct LineTables {
+  SymTab<T, P, Q> Bf;  // interpolation, nodes -> quadrature points
+  SymTab<T, Q, P> Bt;  // its transpose
+  SymTab<T, Q, Q> Df;  // collocated derivative
+  SymTab<T, Q, Q> Dt;  // its transpose
+};
+
+template <typename T, int P, int Q>
+struct LineParams {
+  ApplyParams<T> a;
+  LineTables<T, P, Q> t;
+};
+
+// Host: split a row-major M[NO][NI] (FP64) into the table.
+template <typename T, int NI, int NO>
+inline void make_symtab(const double *M, SymTab<T, NI, NO> &s) {
+  constexpr int HI = NI / 2, HO = NO / 2;
+  for (int k = 0; k <= HO && k < NO; k++) {
+    for (int a = 0; a < (HI > 0 ? HI : 1); a++) {
+      if (a < HI) {
+        s.e[k][a] = (T)(0.5 * (M[k * NI + a] + M[k * NI + NI - 1 - a]));
+        s.o[k][a] = (T)(0.5 * (M[k * NI + a] - M[k * NI + NI - 1 - a]));
+      } else {
+        s.e[k][a] = (T)0;
+        s.o[k][a] = (T)0;
+      }
+    }
+    s.mid[k] = (NI % 2 == 1) ? (T)M[k * NI + HI] : (T)0;
+  }
+}
+
+// Shared memory: 4 cubes of q^3 per element slot.
+template <typename T, int Q, int EPB>
+constexpr size_t lines_smem_bytes() {
+  return sizeof(T) * (size_t)EPB * 4 * Q * Q * Q;
+}
+
+template <typename T, int P, int Q, bool COLLOC, int EPB>
+__device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
+                                                  const LineTables<T, P, Q> &tb, int64_t g,
+                                                  T *cubes, double &dot) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P2 = P * P, P3 = P * P * P;
+  const int slot_raw = threadIdx.x / Q2;
+  const bool live = slot_raw < EPB;
+  const int slot = live ? slot_raw : EPB - 1;
+  const int t = threadIdx.x - slot_raw * Q2;   // thread within the element
+  T *c1 = cubes + (size_t)slot * 4 * Q3, *c2 = c1 + Q3, *c3 = c2 + Q3, *c4 = c3 + Q3;
+  const int64_t N = prm.N;
+  const int64_t k_el = g * EPB + slot_raw;
+  const bool valid = live && (k_el < prm.nsel);
+  int64_t e = 0;
+  if (valid) e = prm.list ? (int64_t)prm.list[k_el] : k_el;
+  const int32_t *en = prm.elem_nodes + e * P3;
+  const T *qd = prm.qdata + e * (int64_t)(6 * Q3);
+  // line coordinates of this thread: (t % Q, t / Q) for q-by-q line sets,
+  // (t % P, t / P) for P-by-q, (t % P, t / P) for P-by-P
+  const int lq0 = t % Q, lq1 = t / Q;
+  const int lp0 = t % P, lp1 = t / P;
+  const bool on_qq = live;                  // t < Q^2 always
+  const bool on_pq = live && t < P * Q;
+  const bool on_pp = live && t < P2;
+  for (int c = 0; c < prm.ncomp; c++) {
+    const T *xc = prm.x + c * N;
+    T *yc = prm.y + c * N;
+    // ---- gather the z-column (a, b) = (lp0, lp1) of the element
+    T u[P];
+#pragma unroll
+    for (int k = 0; k < P; k++)
+      u[k] = (valid && on_pp) ? gather_load(&xc[en[lp0 + P * lp1 + P2 * k]], prm.x_l2_only) : T(0);
+    // c3 holds the values at the quadrature points, x-contiguous [k][j][i]
+    if constexpr (COLLOC) {
+      if (on_pp) {
+#pragma unroll
+        for (int k = 0; k < Q; k++) c3[(k * Q + lp1) * Q + lp0] = u[k];
+      }
+    } else {
+      // z-interpolation of the column (a, b)
+      if (on_pp) {
+        T w[Q];
+        sym_apply<+1>(tb.Bf, u, w);
+#pragma unroll
+        for (int k = 0; k < Q; k++) c1[(k * Q + lp1) * Q + lp0] = w[k];
+      }
+      __syncthreads();
+      // y-lines (a, kq): c1[kq][0..P)[a] -> c2[kq][0..Q)[a]
+      if (on_pq) {
+        T in[P], out[Q];
+#pragma unroll
+        for (int j = 0; j < P; j++) in[j] = c1[(lp1 * Q + j) * Q + lp0];
+        sym_apply<+1>(tb.Bf, in, out);
+#pragma unroll
+        for (int j = 0; j < Q; j++) c2[(lp1 * Q + j) * Q + lp0] = out[j];
+      }
+      __syncthreads();
+      // x-lines (jq, kq): c2[kq][jq][0..P) -> c3[kq][jq][0..Q)
+      if (on_qq) {
+        T in[P], out[Q];
+#pragma unroll
+        for (int i = 0; i < P; i++) in[i] = c2[(lq1 * Q + lq0) * Q + i];
+        sym_apply<+1>(tb.Bf, in, out);
+#pragma unroll
+        for (int i = 0; i < Q; i++) c3[(lq1 * Q + lq0) * Q + i] = out[i];
+      }
+    }
+    __syncthreads();
+    // ---- reference gradients: x into c1, y into c2, z into c4
+    if (on_qq) {
+      T in[Q], out[Q];
+      // x-line (jq, kq) = (lq0, lq1)
+#pragma unroll
+      for (int m = 0; m < Q; m++) in[m] = c3[(lq1 * Q + lq0) * Q + m];
+      sym_apply<-1>(tb.Df, in, out);
+#pragma unroll
+      for (int m = 0; m < Q; m++) c1[(lq1 * Q + lq0) * Q + m] = out[m];
+      // y-line (iq, kq) = (lq0, lq1)
+#pragma unroll
+      for (int m = 0; m < Q; m++) in[m] = c3[(lq1 * Q + m) * Q + lq0];
+      sym_apply<-1>(tb.Df, in, out);
+#pragma unroll
+      for (int m = 0; m < Q; m++) c2[(lq1 * Q + m) * Q + lq0] = out[m];
+      // z-line (iq, jq) = (lq0, lq1)
+#pragma unroll
+      for (int m = 0; m < Q; m++) in[m] = c3[(m * Q + lq1) * Q + lq0];
+      sym_apply<-1>(tb.Df, in, out);
+#pragma unroll
+      for (int m = 0; m < Q; m++) c4[(m * Q + lq1) * Q + lq0] = out[m];
+    }
+    __syncthreads();
+    // ---- pointwise D at the column (iq, jq) = (lq0, lq1), in place
+    if (on_qq) {
+#pragma unroll
+      for (int kq = 0; kq < Q; kq++) {
+        const int pt = (kq * Q + lq1) * Q + lq0;
+        T G00 = 0, G11 = 0, G22 = 0, G12 = 0, G02 = 0, G01 = 0;
+        if (valid) {
+          const T *qk = qd + pt;
+          G00 = qk[0]; G11 = qk[Q3]; G22 = qk[2 * Q3];
+          G12 = qk[3 * Q3]; G02 = qk[4 * Q3]; G01 = qk[5 * Q3];
+        }
+        const T gx = c1[pt], gy = c2[pt], gz = c4[pt];
+        c1[pt] = G00 * gx + G01 * gy + G02 * gz;
+        c2[pt] = G01 * gx + G11 * gy + G12 * gz;
+        c4[pt] = G02 * gx + G12 * gy + G22 * gz;
+      }
+    }
+    __syncthreads();
+    // ---- transposed derivatives, each line in place (disjoint cubes)
+    if (on_qq) {
+      T in[Q], out[Q];
+#pragma unroll
+      for (int m = 0; m < Q; m++) in[m] = c1[(lq1 * Q + lq0) * Q + m];
+      sym_apply<-1>(tb.Dt, in, out);
+#pragma unroll
+      for (int m = 0; m < Q; m++) c1[(lq1 * Q + lq0) * Q + m] = out[m];
+#pragma unroll
+      for (int m = 0; m < Q; m++) in[m] = c2[(lq1 * Q + m) * Q + lq0];
+      sym_apply<-1>(tb.Dt, in, out);
+#pragma unroll
+      for (int m = 0; m < Q; m++) c2[(lq1 * Q + m) * Q + lq0] = out[m];
+#pragma unroll
+      for (int m = 0; m < Q; m++) in[m] = c4[(m * Q + lq1) * Q + lq0];
+      sym_apply<-1>(tb.Dt, in, out);
+#pragma unroll
+      for (int m = 0; m < Q; m++) c4[(m * Q + lq1) * Q + lq0] = out[m];
+    }
+    __syncthreads();
+    if constexpr (COLLOC) {
+      // sum of the three contributions at the node column (a, b), scatter
+      if (on_pp) {
+#pragma unroll
+        for (int k = 0; k < P; k++) {
+          const int pt = (k * Q + lp1) * Q + lp0;
+          const T s = c1[pt] + c2[pt] + c4[pt];
+          if (valid) {
+            const int64_t gi = en[lp0 + P * lp1 + P2 * k];
+            atomic_add(&yc[gi], s);
+            dot += (double)s * (double)u[k];
+          }
+        }
+      }
+      // the next component's first writes (c3) and the next gradients
+      // (c1, c2, c4) must not pass these reads
+      __syncthreads();
+    } else {
+      // x-lines (jq, kq): sum of the three, transposed interpolation -> c3[kq][jq][0..P)
+      if (on_qq) {
+        T in[Q], out[P];
+#pragma unroll
+        for (int m = 0; m < Q; m++) {
+          const int pt = (lq1 * Q + lq0) * Q + m;
+          in[m] = c1[pt] + c2[pt] + c4[pt];
+        }
+        sym_apply<+1>(tb.Bt, in, out);
+#pragma unroll
+        for (int i = 0; i < P; i++) c3[(lq1 * Q + lq0) * Q + i] = out[i];
+      }
+      __syncthreads();
+      // y-lines (a, kq): c3[kq][0..Q)[a] -> c1[kq][0..P)[a]
+      if (on_pq) {
+        T in[Q], out[P];
+#pragma unroll
+        for (int j = 0; j < Q; j++) in[j] = c3[(lp1 * Q + j) * Q + lp0];
+        sym_apply<+1>(tb.Bt, in, out);
+#pragma unroll
+        for (int j = 0; j < P; j++) c1[(lp1 * Q + j) * Q + lp0] = out[j];
+      }
+      __syncthreads();
+      // z-lines (a, b): c1[0..Q)[b][a] -> nodes, scatter
+      if (on_pp) {
+        T in[Q], out[P];
+#pragma unroll
+        for (int k = 0; k < Q; k++) in[k] = c1[(k * Q + lp1) * Q + lp0];
+        sym_apply<+1>(tb.Bt, in, out);
+#pragma unroll
+        for (int k = 0; k < P; k++) {
+          if (valid) {
+            const int64_t gi = en[lp0 + P * lp1 + P2 * k];
+            atomic_add(&yc[gi], out[k]);
+            dot += (double)out[k] * (double)u[k];
+          }
+        }
+      }
+      // c1 is the next component's first target
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T, int P, int Q, bool COLLOC, int EPB>
+__global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
+    fem_apply_lines_kernel(const LineParams<T, P, Q> lp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *cubes = reinterpret_cast<T *>(smem_raw);
+  const ApplyParams<T> &prm = lp.a;
+  double dot = 0.0;
+  const int64_t ngroups = (prm.nsel + EPB - 1) / EPB;
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
+    apply_group_lines<T, P, Q, COLLOC, EPB>(prm, lp.t, g, cubes, dot);
+  if (prm.dot_out) {
+    double v[1] = {dot};
+    __shared__ double tot[1];
+    if (fem_grid_sum<1>(v, prm.partials, prm.counter, tot) && threadIdx.x == 0)
+      *prm.dot_out = tot[0];
+  }
+}
+
+}  // namespace fem_apply

