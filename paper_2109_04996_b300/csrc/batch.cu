@@ -31,9 +31,11 @@
 #include <string>
 #include <vector>
 
-#include "apply_kernel.cuh"
+#include "apply_lines.cuh"
 
 using fem_apply::ApplyParams;
+using fem_apply::LineTables;
+using fem_apply::apply_group_lines;
 using fem_apply::Slab;
 using fem_apply::apply_group;
 using fem_apply::apply_smem_bytes;
@@ -46,6 +48,7 @@ struct BatchProblem {
   const float *qdata32, *B32, *Dq32;
   const double *qdata64, *B64, *Dq64;
   const double *diag;
+  const float *ltab32;   // LineTables<float, P, P+1> of this problem (device)
   // outer (FP64) and inner (FP32) vectors
   const double *b;
   double *x, *y64;
@@ -66,6 +69,11 @@ struct BatchSync {
   unsigned count, gen;
   int error;
   int pad;
+};
+
+template <int A, int B>
+struct PQ {
+  static constexpr int first = A, second = B;
 };
 
 struct fem_batch {
@@ -201,6 +209,59 @@ __device__ void batch_group_p(const BatchProblem &pr, int64_t g, const T *x, T *
   }
 }
 
+// FP32 inner apply with the line-based even-odd body: the problem's split
+// tables are copied into shared memory when the block switches problems.
+constexpr int kLineTabBytes = 1024;  // >= sizeof(LineTables<float, 9, 10>)
+
+template <int NT, int P>
+__device__ void batch_group_lines(const BatchProblem &pr, int64_t g, unsigned char *smem,
+                                  double &dot, bool reload) {
+  constexpr int Q = P + 1;
+  constexpr int EPB = BatchEpb<NT, Q>::value;
+  static_assert(sizeof(LineTables<float, P, Q>) <= kLineTabBytes, "line tables too large");
+  auto *tb = reinterpret_cast<LineTables<float, P, Q> *>(smem);
+  float *cubes = reinterpret_cast<float *>(smem + kLineTabBytes);
+  if (reload) {
+    __syncthreads();
+    const float *src = pr.ltab32;
+    float *dst = reinterpret_cast<float *>(tb);
+    for (int i = threadIdx.x; i < (int)(sizeof(LineTables<float, P, Q>) / sizeof(float)); i += blockDim.x)
+      dst[i] = src[i];
+    __syncthreads();
+  }
+  ApplyParams<float> prm;
+  prm.x = pr.p; prm.y = pr.y; prm.elem_nodes = pr.elem_nodes; prm.list = nullptr; prm.nsel = pr.E;
+  prm.N = pr.N; prm.ncomp = pr.ncomp;
+  prm.qdata = pr.qdata32; prm.B = pr.B32; prm.Dq = pr.Dq32;
+  prm.partials = nullptr; prm.counter = nullptr; prm.dot_out = nullptr;
+  prm.x_l2_only = 0;  // written before the last grid barrier (see grid_barrier)
+  apply_group_lines<float, P, Q, false, EPB>(prm, *tb, g, cubes, dot);
+}
+
+template <int NT>
+__device__ void batch_group_lines_p(const BatchProblem &pr, int64_t g, unsigned char *smem,
+                                    double &dot, bool reload) {
+  switch (pr.P) {
+    case 2: batch_group_lines<NT, 2>(pr, g, smem, dot, reload); break;
+    case 3: batch_group_lines<NT, 3>(pr, g, smem, dot, reload); break;
+    case 4: batch_group_lines<NT, 4>(pr, g, smem, dot, reload); break;
+    case 5: batch_group_lines<NT, 5>(pr, g, smem, dot, reload); break;
+    case 6: batch_group_lines<NT, 6>(pr, g, smem, dot, reload); break;
+    case 7: batch_group_lines<NT, 7>(pr, g, smem, dot, reload); break;
+    case 8: batch_group_lines<NT, 8>(pr, g, smem, dot, reload); break;
+    case 9: batch_group_lines<NT, 9>(pr, g, smem, dot, reload); break;
+  }
+}
+
+template <int NT>
+constexpr size_t batch_lines_smem() {
+  size_t m = 0;
+#define FEM_BL(P) { size_t s = fem_apply::lines_smem_bytes<float, P + 1, BatchEpb<NT, P + 1>::value>(); if (s > m) m = s; }
+  FEM_BL(2) FEM_BL(3) FEM_BL(4) FEM_BL(5) FEM_BL(6) FEM_BL(7) FEM_BL(8) FEM_BL(9)
+#undef FEM_BL
+  return kLineTabBytes + m;
+}
+
 template <typename T, int NT>
 constexpr size_t batch_smem() {
   size_t m = 0;
@@ -253,7 +314,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         dot = 0.0;
       }
       const BatchProblem &pr = a.prob[i];
-      batch_group_p<float, NT>(pr, it - a.gstart[i], pr.p, pr.y, smem, dot, i != cur_prob);
+      batch_group_lines_p<NT>(pr, it - a.gstart[i], smem, dot, i != cur_prob);
       cur_prob = i;
     }
     if (cur_prob >= 0) {
@@ -432,7 +493,7 @@ const int kNtChoices[3] = {128, 256, 512};
 template <int NT>
 int launch_inner_nt(fem_batch *b, const BatchArgs &a, int bps) {
   auto kern = batch_inner_kernel<NT>;
-  constexpr size_t smem = batch_smem<float, NT>();
+  constexpr size_t smem = batch_lines_smem<NT>();
   FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -572,8 +633,34 @@ extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **ou
     p.qdata64 = op->d_qdata; p.B64 = op->d_B; p.Dq64 = op->d_Dq;
     p.diag = op->d_diag;
     p.b = nullptr; p.x = nullptr;
+    {
+      // split tables of the line-based body, built on the host from FP64
+      std::vector<unsigned char> blob(kLineTabBytes, 0);
+      double Bt[FEM_MAX_P * FEM_MAX_Q], Dt[FEM_MAX_Q * FEM_MAX_Q];
+      const int P_ = op->P, Q_ = op->Q;
+      for (int k = 0; k < Q_; k++)
+        for (int a2 = 0; a2 < P_; a2++) Bt[a2 * Q_ + k] = op->tab.B[k * P_ + a2];
+      for (int k = 0; k < Q_; k++)
+        for (int m2 = 0; m2 < Q_; m2++) Dt[m2 * Q_ + k] = op->tab.Dq[k * Q_ + m2];
+      auto fill = [&](auto *lt, auto pq) {
+        constexpr int PP_ = decltype(pq)::first, QQ_ = decltype(pq)::second;
+        fem_apply::make_symtab<float, PP_, QQ_>(op->tab.B, lt->Bf);
+        fem_apply::make_symtab<float, QQ_, PP_>(Bt, lt->Bt);
+        fem_apply::make_symtab<float, QQ_, QQ_>(op->tab.Dq, lt->Df);
+        fem_apply::make_symtab<float, QQ_, QQ_>(Dt, lt->Dt);
+      };
+      switch (P_) {
+#define FEM_LT(PV) case PV: fill(reinterpret_cast<LineTables<float, PV, PV + 1> *>(blob.data()), PQ<PV, PV + 1>()); break;
+        FEM_LT(2) FEM_LT(3) FEM_LT(4) FEM_LT(5) FEM_LT(6) FEM_LT(7) FEM_LT(8) FEM_LT(9)
+#undef FEM_LT
+      }
+      float *dt = nullptr;
+      ok = dalloc((void **)&dt, kLineTabBytes) &&
+           cudaMemcpy(dt, blob.data(), kLineTabBytes, cudaMemcpyHostToDevice) == cudaSuccess;
+      p.ltab32 = dt;
+    }
     const size_t nn = (size_t)p.n;
-    ok = dalloc((void **)&p.y64, 8 * nn) && dalloc((void **)&p.r, 4 * nn) &&
+    ok = ok && dalloc((void **)&p.y64, 8 * nn) && dalloc((void **)&p.r, 4 * nn) &&
          dalloc((void **)&p.z, 4 * nn) && dalloc((void **)&p.p, 4 * nn) &&
          dalloc((void **)&p.y, 4 * nn) && dalloc((void **)&p.d, 4 * nn) &&
          dalloc((void **)&p.dinv, 4 * nn);
