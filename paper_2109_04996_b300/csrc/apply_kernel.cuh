@@ -41,6 +41,35 @@ struct ApplyParams {
   double *dot_out;
   int x_l2_only = 0;          // 1: gather x with L2-only loads (x written by
                               // other blocks of a persistent kernel)
+  int want_dot = 0;           // 1: accumulate x.y into the caller's `dot` even
+                              // without dot_out (persistent batch kernel)
+};
+
+// Accumulator of a thread's share of x.y over one element.  FP64: plain.
+// FP32: compensated (double-float) on the FP32 pipe -- each product is split
+// exactly, a*b = p + e (FMA), p is added to hi by TwoSum and the rounding
+// errors are collected in lo (Dekker 1971; Ogita, Rump & Oishi 2005) -- so
+// that the FP32 kernel neither loses p^T A p to cancellation between a node's
+// terms nor uses the 1/64-rate FP64 pipe per term.
+template <typename T>
+struct DotAcc {
+  T v = 0;
+  __device__ __forceinline__ void add(T a, T b) { v += a * b; }
+  __device__ __forceinline__ double get() const { return (double)v; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + e;
+  }
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
 template <typename T>
@@ -171,6 +200,9 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
     cp_async_commit();
     qd = sl.sq + sl.slot * 6 * Q3 + (ty * Q + tx);
   }
+  // this thread's share of x.y over the group (see DotAcc), added to the
+  // FP64 `dot` once
+  DotAcc<T> dl;
     for (int c = 0; c < prm.ncomp; c++) {
       const T *xc = prm.x + c * N;
       T *yc = prm.y + c * N;
@@ -183,7 +215,7 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
             const T xv = gather_load(&xc[gi], prm.x_l2_only);
             const T v = qd[k * Q2] * xv;
             atomic_add(&yc[gi], v);
-            dot += (double)v * (double)xv;
+            dl.add(v, xv);
           }
         }
       } else if constexpr (COLLOC) {
@@ -249,7 +281,7 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
           if (valid) {
             const int64_t gi = en[tx + P * ty + P2 * k];
             atomic_add(&yc[gi], s);
-            dot += (double)s * (double)u[k];
+            dl.add(s, u[k]);
           }
         }
       } else {
@@ -406,12 +438,13 @@ __device__ __forceinline__ void apply_group(const ApplyParams<T> &prm, int64_t g
             if (valid) {
               const int64_t gi = en[tx + P * ty + P2 * k];
               atomic_add(&yc[gi], s);
-              dot += (double)s * (double)r[k];
+              dl.add(s, r[k]);
             }
           }
         }
       }
     }
+  if (prm.dot_out || prm.want_dot) dot += dl.get();
 }
 
 template <typename T, int P, int Q, int KIND, bool COLLOC, int EPB>

@@ -132,6 +132,9 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   const bool on_qq = live;                  // t < Q^2 always
   const bool on_pq = live && t < P * Q;
   const bool on_pp = live && t < P2;
+  // this thread's share of x.y over the group (see DotAcc), added to the
+  // FP64 `dot` once
+  DotAcc<T> dl;
   for (int c = 0; c < prm.ncomp; c++) {
     const T *xc = prm.x + c * N;
     T *yc = prm.y + c * N;
@@ -247,7 +250,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
           if (valid) {
             const int64_t gi = en[lp0 + P * lp1 + P2 * k];
             atomic_add(&yc[gi], s);
-            dot += (double)s * (double)u[k];
+            dl.add(s, u[k]);
           }
         }
       }
@@ -289,7 +292,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
           if (valid) {
             const int64_t gi = en[lp0 + P * lp1 + P2 * k];
             atomic_add(&yc[gi], out[k]);
-            dot += (double)out[k] * (double)u[k];
+            dl.add(out[k], u[k]);
           }
         }
       }
@@ -297,6 +300,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       __syncthreads();
     }
   }
+  if (prm.dot_out || prm.want_dot) dot += dl.get();
 }
 
 template <typename T, int P, int Q, bool COLLOC, int EPB>

@@ -235,6 +235,7 @@ __device__ void batch_group_lines(const BatchProblem &pr, int64_t g, unsigned ch
   prm.qdata = pr.qdata32; prm.B = pr.B32; prm.Dq = pr.Dq32;
   prm.partials = nullptr; prm.counter = nullptr; prm.dot_out = nullptr;
   prm.x_l2_only = 0;  // written before the last grid barrier (see grid_barrier)
+  prm.want_dot = 1;   // p^T A p of the problem
   apply_group_lines<float, P, Q, false, EPB>(prm, *tb, g, cubes, dot);
 }
 
