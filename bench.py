@@ -134,12 +134,35 @@ def measured_peaks():
 
 def fp64_peak_tflops(sm_mhz):
     """FP64 FMA peak derived from unit counts and clock: 148 SMs x 2 FP64 FMA
-    lanes... per SM per clock x 2 flops; see the design doc (the B300 nominal is
-    1.25 TFLOP/s)."""
+    per SM per clock x 2 flops x the SM clock (1.20 TFLOP/s at 2032 MHz; the
+    B300 nominal is 1.25 TFLOP/s)."""
     return 148 * FP64_FMA_PER_SM_CLK * 2 * (sm_mhz or 2032.0) * 1e6 / 1e12
 
 
 FP64_FMA_PER_SM_CLK = 2.0
+
+# DRAM bytes of one FP64 BP3 apply per order, from one ncu capture
+# (dram__bytes_read.sum, dram__bytes_write.sum) of `bench.py --profile
+# BP3:<p>:f64 --dofs 4e6` on a B300: (E, N, read, write) of the captured mesh.
+# The ratio to the algorithmic bytes (1.03-1.07) is steady across sizes (the
+# bytes are qdata, indices and the two vectors, all proportional to the mesh),
+# so the full-size traffic is that ratio times the full-size algorithmic bytes.
+APPLY_F64_DRAM = {
+    1: (3944312, 4019679, 5374304000, 68418816),
+    2: (493039, 4019679, 1661111040, 46400512),
+    3: (148877, 4096000, 1006866432, 36539136),
+    4: (59319, 3869893, 712461824, 31814656),
+    5: (32768, 4173281, 634934272, 30916352),
+    6: (17576, 3869893, 524028416, 30568960),
+    7: (12167, 4251528, 523802624, 31756288),
+    8: (8000, 4173281, 476999936, 30838272),
+}
+
+
+def dram_ratio(p):
+    E, N, rd, wr = APPLY_F64_DRAM[p]
+    P, q = p + 1, p + 2
+    return (rd + wr) / (16 * N + 4 * E * P ** 3 + 48 * E * q ** 3)
 
 
 def cpu_baseline(work, iters, seconds, seed=0):
@@ -570,7 +593,7 @@ def main():
 
     # dominant kernel: the fused apply, timed per launch with events on its stream
     per_p = []
-    tot_time, tot_flop, tot_bytes = 0.0, 0.0, 0.0
+    tot_time, tot_flop, tot_bytes, tot_traffic = 0.0, 0.0, 0.0, 0.0
     for p, n, gm, op, b, x in ops:
         y = torch.empty_like(x)
         for _ in range(3):
@@ -589,17 +612,21 @@ def main():
                       "apply_tflops": fl / t_apply / 1e12,
                       "apply_hbm_gbs": by / t_apply / 1e9})
         tot_time += t_apply; tot_flop += fl; tot_bytes += by
+        tot_traffic += dram_ratio(p) * by
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     fp64_peak = fp64_peak_tflops(clocks.get("sm_mhz"))
     achieved = tot_flop / tot_time / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "kernel": "fem_apply_kernel (FP64, all orders of the sweep)",
+                "frac": achieved / fp64_peak, "traffic": tot_traffic,
+                "traffic_note": "DRAM bytes of one sweep (one FP64 apply per order), ncu counters"
+                                " of a 4e6-DOF capture per order scaled by algorithmic bytes",
+                "algorithmic_bytes": tot_bytes,
+                "kernel": "FP64 fused apply (slab body p<=5, line body p>=6), all orders",
                 "hbm_achieved_gbs": tot_bytes / tot_time / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": tot_bytes / tot_time / 1e9 / hbm_peak,
-                "peak_source": "FP64 peak derived from unit counts x median SM clock (DESIGN.md);"
-                               " HBM from MEASURED_PEAKS.json"}
+                "peak_source": "FP64 peak = 148 SMs x 2 FMA/clk x 2 flop x median SM clock;"
+                               " HBM peak of measured (MEASURED_PEAKS.json)"}
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -326,7 +326,9 @@ fem_status fem_precond_apply(fem_precond *pc, const float *r, float *z);
 /* Flexible CG (Notay 2000, one stored direction) with preconditioner B as
  * the inner FP32 solve of FP64 iterative refinement (as fem_solve_refined).
  * Each outer step is one CUDA graph; the learned correction sits in a
- * conditional IF node.  Fallback: every 64 inner iterations the residual
+ * conditional IF node.  The direction carries over between outer steps with
+ * its preconditioned-residual part replaced (p += z_new - z_old), so with the
+ * Jacobi part alone the iteration counts track fem_solve_refined.  Fallback: every 64 inner iterations the residual
  * must have dropped 4x, else the learned part is switched off for the rest
  * of the solve (stats->fallback = 1), which then is Jacobi-PCG.  opts: rtol,
  * inner_rtol, maxit, max_outer (precond is implied).  Synchronizes. */

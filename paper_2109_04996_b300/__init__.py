@@ -480,7 +480,7 @@ class Precond:
         _check(lib().fem_precond_apply(self._h, _ptr(r), _ptr(z)))
         return z
 
-    def fcg(self, b, x, rtol=1e-10, inner_rtol=1e-5, maxit=100000, max_outer=20):
+    def fcg(self, b, x, rtol=1e-10, inner_rtol=0.1, maxit=100000, max_outer=100):
         o = _CgOpts(PC_LEARNED, int(maxit), float(rtol), 1, float(inner_rtol), int(max_outer))
         st = _CgStats()
         rc = lib().fem_fcg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))

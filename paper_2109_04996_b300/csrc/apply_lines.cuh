@@ -72,6 +72,7 @@ __device__ __forceinline__ void sym_apply(const SymTab<T, NI, NO> &M, const T (&
 
 template <typename T, int P, int Q>
 struct LineTables {
+  static constexpr int kP = P, kQ = Q;
   SymTab<T, P, Q> Bf;  // interpolation, nodes -> quadrature points
   SymTab<T, Q, P> Bt;  // its transpose
   SymTab<T, Q, Q> Df;  // collocated derivative

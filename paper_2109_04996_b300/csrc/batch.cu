@@ -29,6 +29,7 @@
 #include <string.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "apply_lines.cuh"
@@ -48,7 +49,6 @@ struct BatchProblem {
   const float *qdata32, *B32, *Dq32;
   const double *qdata64, *B64, *Dq64;
   const double *diag;
-  const float *ltab32;   // LineTables<float, P, P+1> of this problem (device)
   // outer (FP64) and inner (FP32) vectors
   const double *b;
   double *x, *y64;
@@ -69,11 +69,6 @@ struct BatchSync {
   unsigned count, gen;
   int error;
   int pad;
-};
-
-template <int A, int B>
-struct PQ {
-  static constexpr int first = A, second = B;
 };
 
 struct fem_batch {
@@ -209,26 +204,42 @@ __device__ void batch_group_p(const BatchProblem &pr, int64_t g, const T *x, T *
   }
 }
 
-// FP32 inner apply with the line-based even-odd body: the problem's split
-// tables are copied into shared memory when the block switches problems.
-constexpr int kLineTabBytes = 1024;  // >= sizeof(LineTables<float, 9, 10>)
+// FP32 inner apply with the line-based even-odd body.  The split tables of
+// a BP3-type problem depend on its order alone (Gauss-Legendre, q = p+2), so
+// one set per order lives in constant memory and is read like the kernel
+// parameters of the single-operator kernel: operands of the FMAs, not values
+// held in registers.  fem_batch_create writes the slots of the orders it
+// holds (the same values for every batch, so concurrent batches agree).
+struct BatchLineTables {
+  LineTables<float, 2, 3> t2;
+  LineTables<float, 3, 4> t3;
+  LineTables<float, 4, 5> t4;
+  LineTables<float, 5, 6> t5;
+  LineTables<float, 6, 7> t6;
+  LineTables<float, 7, 8> t7;
+  LineTables<float, 8, 9> t8;
+  LineTables<float, 9, 10> t9;
+};
+__constant__ BatchLineTables c_ltab;
+
+template <int P>
+__device__ __forceinline__ const LineTables<float, P, P + 1> &batch_ltab() {
+  if constexpr (P == 2) return c_ltab.t2;
+  else if constexpr (P == 3) return c_ltab.t3;
+  else if constexpr (P == 4) return c_ltab.t4;
+  else if constexpr (P == 5) return c_ltab.t5;
+  else if constexpr (P == 6) return c_ltab.t6;
+  else if constexpr (P == 7) return c_ltab.t7;
+  else if constexpr (P == 8) return c_ltab.t8;
+  else return c_ltab.t9;
+}
 
 template <int NT, int P>
 __device__ void batch_group_lines(const BatchProblem &pr, int64_t g, unsigned char *smem,
-                                  double &dot, bool reload) {
+                                  double &dot) {
   constexpr int Q = P + 1;
   constexpr int EPB = BatchEpb<NT, Q>::value;
-  static_assert(sizeof(LineTables<float, P, Q>) <= kLineTabBytes, "line tables too large");
-  auto *tb = reinterpret_cast<LineTables<float, P, Q> *>(smem);
-  float *cubes = reinterpret_cast<float *>(smem + kLineTabBytes);
-  if (reload) {
-    __syncthreads();
-    const float *src = pr.ltab32;
-    float *dst = reinterpret_cast<float *>(tb);
-    for (int i = threadIdx.x; i < (int)(sizeof(LineTables<float, P, Q>) / sizeof(float)); i += blockDim.x)
-      dst[i] = src[i];
-    __syncthreads();
-  }
+  float *cubes = reinterpret_cast<float *>(smem);
   ApplyParams<float> prm;
   prm.x = pr.p; prm.y = pr.y; prm.elem_nodes = pr.elem_nodes; prm.list = nullptr; prm.nsel = pr.E;
   prm.N = pr.N; prm.ncomp = pr.ncomp;
@@ -236,21 +247,21 @@ __device__ void batch_group_lines(const BatchProblem &pr, int64_t g, unsigned ch
   prm.partials = nullptr; prm.counter = nullptr; prm.dot_out = nullptr;
   prm.x_l2_only = 0;  // written before the last grid barrier (see grid_barrier)
   prm.want_dot = 1;   // p^T A p of the problem
-  apply_group_lines<float, P, Q, false, EPB>(prm, *tb, g, cubes, dot);
+  apply_group_lines<float, P, Q, false, EPB>(prm, batch_ltab<P>(), g, cubes, dot);
 }
 
 template <int NT>
 __device__ void batch_group_lines_p(const BatchProblem &pr, int64_t g, unsigned char *smem,
-                                    double &dot, bool reload) {
+                                    double &dot) {
   switch (pr.P) {
-    case 2: batch_group_lines<NT, 2>(pr, g, smem, dot, reload); break;
-    case 3: batch_group_lines<NT, 3>(pr, g, smem, dot, reload); break;
-    case 4: batch_group_lines<NT, 4>(pr, g, smem, dot, reload); break;
-    case 5: batch_group_lines<NT, 5>(pr, g, smem, dot, reload); break;
-    case 6: batch_group_lines<NT, 6>(pr, g, smem, dot, reload); break;
-    case 7: batch_group_lines<NT, 7>(pr, g, smem, dot, reload); break;
-    case 8: batch_group_lines<NT, 8>(pr, g, smem, dot, reload); break;
-    case 9: batch_group_lines<NT, 9>(pr, g, smem, dot, reload); break;
+    case 2: batch_group_lines<NT, 2>(pr, g, smem, dot); break;
+    case 3: batch_group_lines<NT, 3>(pr, g, smem, dot); break;
+    case 4: batch_group_lines<NT, 4>(pr, g, smem, dot); break;
+    case 5: batch_group_lines<NT, 5>(pr, g, smem, dot); break;
+    case 6: batch_group_lines<NT, 6>(pr, g, smem, dot); break;
+    case 7: batch_group_lines<NT, 7>(pr, g, smem, dot); break;
+    case 8: batch_group_lines<NT, 8>(pr, g, smem, dot); break;
+    case 9: batch_group_lines<NT, 9>(pr, g, smem, dot); break;
   }
 }
 
@@ -260,7 +271,7 @@ constexpr size_t batch_lines_smem() {
 #define FEM_BL(P) { size_t s = fem_apply::lines_smem_bytes<float, P + 1, BatchEpb<NT, P + 1>::value>(); if (s > m) m = s; }
   FEM_BL(2) FEM_BL(3) FEM_BL(4) FEM_BL(5) FEM_BL(6) FEM_BL(7) FEM_BL(8) FEM_BL(9)
 #undef FEM_BL
-  return kLineTabBytes + m;
+  return m;
 }
 
 template <typename T, int NT>
@@ -300,8 +311,8 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         a.sc[i].rr[cur] = 0.0;
       }
     }
-    // a block's items of one problem are consecutive in its stride: tables
-    // are loaded and p^T A p is flushed once per problem, not per item
+    // a block's items of one problem are consecutive in its stride: p^T A p
+    // is flushed once per problem, not per item
     int cur_prob = -1;
     double dot = 0.0;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -315,7 +326,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         dot = 0.0;
       }
       const BatchProblem &pr = a.prob[i];
-      batch_group_lines_p<NT>(pr, it - a.gstart[i], smem, dot, i != cur_prob);
+      batch_group_lines_p<NT>(pr, it - a.gstart[i], smem, dot);
       cur_prob = i;
     }
     if (cur_prob >= 0) {
@@ -624,6 +635,8 @@ extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **ou
             dalloc((void **)&b->d_cstart, sizeof(int64_t) * (n + 1));
   b->h_prob.resize(n);
   std::vector<int64_t> cs(n + 1, 0), g64(n + 1, 0);
+  BatchLineTables htab;   // host image of the constant tables (uploaded per slot)
+  bool have_tab[FEM_MAX_P + 1] = {};
   for (int i = 0; ok && i < n; i++) {
     const fem_op *op = ops[i];
     BatchProblem &p = b->h_prob[i];
@@ -634,31 +647,39 @@ extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **ou
     p.qdata64 = op->d_qdata; p.B64 = op->d_B; p.Dq64 = op->d_Dq;
     p.diag = op->d_diag;
     p.b = nullptr; p.x = nullptr;
-    {
+    if (!have_tab[op->P]) {
       // split tables of the line-based body, built on the host from FP64
-      std::vector<unsigned char> blob(kLineTabBytes, 0);
+      have_tab[op->P] = true;
       double Bt[FEM_MAX_P * FEM_MAX_Q], Dt[FEM_MAX_Q * FEM_MAX_Q];
       const int P_ = op->P, Q_ = op->Q;
       for (int k = 0; k < Q_; k++)
         for (int a2 = 0; a2 < P_; a2++) Bt[a2 * Q_ + k] = op->tab.B[k * P_ + a2];
       for (int k = 0; k < Q_; k++)
         for (int m2 = 0; m2 < Q_; m2++) Dt[m2 * Q_ + k] = op->tab.Dq[k * Q_ + m2];
-      auto fill = [&](auto *lt, auto pq) {
-        constexpr int PP_ = decltype(pq)::first, QQ_ = decltype(pq)::second;
-        fem_apply::make_symtab<float, PP_, QQ_>(op->tab.B, lt->Bf);
-        fem_apply::make_symtab<float, QQ_, PP_>(Bt, lt->Bt);
-        fem_apply::make_symtab<float, QQ_, QQ_>(op->tab.Dq, lt->Df);
-        fem_apply::make_symtab<float, QQ_, QQ_>(Dt, lt->Dt);
+      auto fill = [&](auto &lt) {
+        using LT = typename std::remove_reference<decltype(lt)>::type;
+        constexpr int PP_ = LT::kP, QQ_ = LT::kQ;
+        fem_apply::make_symtab<float, PP_, QQ_>(op->tab.B, lt.Bf);
+        fem_apply::make_symtab<float, QQ_, PP_>(Bt, lt.Bt);
+        fem_apply::make_symtab<float, QQ_, QQ_>(op->tab.Dq, lt.Df);
+        fem_apply::make_symtab<float, QQ_, QQ_>(Dt, lt.Dt);
+        const size_t off = (size_t)((const unsigned char *)&lt - (const unsigned char *)&htab);
+        if (ok && cudaMemcpyToSymbolAsync(c_ltab, &lt, sizeof(LT), off, cudaMemcpyHostToDevice,
+                                          b->stream) != cudaSuccess) {
+          cudaGetLastError();
+          ok = false;
+        }
       };
       switch (P_) {
-#define FEM_LT(PV) case PV: fill(reinterpret_cast<LineTables<float, PV, PV + 1> *>(blob.data()), PQ<PV, PV + 1>()); break;
-        FEM_LT(2) FEM_LT(3) FEM_LT(4) FEM_LT(5) FEM_LT(6) FEM_LT(7) FEM_LT(8) FEM_LT(9)
-#undef FEM_LT
+        case 2: fill(htab.t2); break;
+        case 3: fill(htab.t3); break;
+        case 4: fill(htab.t4); break;
+        case 5: fill(htab.t5); break;
+        case 6: fill(htab.t6); break;
+        case 7: fill(htab.t7); break;
+        case 8: fill(htab.t8); break;
+        case 9: fill(htab.t9); break;
       }
-      float *dt = nullptr;
-      ok = dalloc((void **)&dt, kLineTabBytes) &&
-           cudaMemcpy(dt, blob.data(), kLineTabBytes, cudaMemcpyHostToDevice) == cudaSuccess;
-      p.ltab32 = dt;
     }
     const size_t nn = (size_t)p.n;
     ok = ok && dalloc((void **)&p.y64, 8 * nn) && dalloc((void **)&p.r, 4 * nn) &&

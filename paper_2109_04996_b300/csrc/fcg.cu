@@ -10,7 +10,8 @@
 //   alpha_k = p_k^T r_k / p_k^T A p_k.
 // It runs as the inner FP32 solve of FP64 iterative refinement, as in
 // refine.cu: each outer step is one CUDA graph (FP64 residual, preconditioner
-// of r_0, conditional WHILE over the FCG body, FP64 correction).
+// of r_0, conditional WHILE over the FCG body, FP64 correction), and the
+// direction carries over from one outer step to the next.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -203,11 +204,15 @@ __device__ __forceinline__ bool learned_active(const FcgScalars *s) {
   return !s->fallback && s->gamma != 0.0;
 }
 
-__global__ void f_prepare_kernel(double *x, double *y64, const uint8_t *dir, int64_t N, int64_t n) {
+// start of a solve: Dirichlet entries of x, the FP64 scratch, and the inner
+// direction state (p = z = y = 0, so the first outer step starts with p = z)
+__global__ void f_prepare_kernel(double *x, double *y64, float *p, float *z, float *y,
+                                 const uint8_t *dir, int64_t N, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (dir && dir[i % N]) x[i] = 0.0;
     y64[i] = 0.0;
+    p[i] = 0.0f; z[i] = 0.0f; y[i] = 0.0f;
   }
 }
 
@@ -218,7 +223,10 @@ __global__ void f_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N,
 }
 
 // outer residual; inner start r = r64, d = 0, y = 0, z = dinv r (the learned
-// part is added by the preconditioner kernels that follow)
+// part is added by the preconditioner kernels that follow).  The direction is
+// kept across outer steps with its preconditioned-residual part swapped
+// (reliable update, as in refine.cu): here p -= z_old, and
+// f_restart_kernel adds the new z once it is complete.
 __global__ void f_residual_kernel(const FParams c) {
   double v[3] = {0, 0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
@@ -227,7 +235,8 @@ __global__ void f_residual_kernel(const FParams c) {
     const double bi = fixed ? 0.0 : c.b[i];
     const double r64 = fixed ? 0.0 : bi - c.y64[i];
     const float r = (float)r64;
-    c.r[i] = r; c.z[i] = c.dinv[i] * r; c.d[i] = 0.0f; c.y[i] = 0.0f; c.p[i] = 0.0f;
+    c.p[i] -= c.z[i];
+    c.r[i] = r; c.z[i] = c.dinv[i] * r; c.d[i] = 0.0f; c.y[i] = 0.0f;
     c.y64[i] = 0.0;
     v[0] += r64 * r64; v[1] += bi * bi; v[2] += (double)r * r;
   }
@@ -266,6 +275,21 @@ __global__ void f_direction_kernel(const FParams c) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float pv = c.z[i] + beta * c.p[i];
+    c.p[i] = pv;
+    c.y[i] = 0.0f;
+    v[0] += (double)pv * (double)c.r[i];
+  }
+  __shared__ double tot[1];
+  if (fem_grid_sum<1>(v, c.partials, c.counter, tot) && threadIdx.x == 0) c.sc->pr = tot[0];
+}
+
+// first direction of an outer step: p += z (z complete, learned part
+// included; p held p_old - z_old); y = 0; pr = p^T r
+__global__ void f_restart_kernel(const FParams c) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float pv = c.p[i] + c.z[i];
     c.p[i] = pv;
     c.y[i] = 0.0f;
     v[0] += (double)pv * (double)c.r[i];
@@ -439,7 +463,7 @@ int build_graph(fem_precond *pc, const double *b, double *x) {
     if (pc->mlp) {
       if ((rc = add_learned_if(pc, pc->cap, pc->cap3, hl0, &e))) break;
     }
-    f_direction_kernel<<<g, kT, 0, pc->cap>>>(c);  // p_0 = z_0, pr
+    f_restart_kernel<<<g, kT, 0, pc->cap>>>(c);  // p = p_old + (z - z_old), pr
     e = cudaStreamGetCaptureInfo(pc->cap, &st, nullptr, &graph, &deps, nullptr, &ndeps);
     if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
     cudaGraphNodeParams cp = {};
@@ -626,7 +650,8 @@ extern "C" fem_status fem_fcg_solve(fem_precond *pc, const double *b, double *x,
   init.gamma = pc->mlp ? pc->gamma : 0.0;
   FEM_CUDA_TRY(cudaMemcpyAsync(pc->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   f_dinv_kernel<<<gridn(pc->n), kT, 0, s>>>(op->d_diag, op->mesh->d_dirichlet, pc->N, pc->n, pc->dinv);
-  f_prepare_kernel<<<gridn(pc->n), kT, 0, s>>>(x, pc->y64, op->mesh->d_dirichlet, pc->N, pc->n);
+  f_prepare_kernel<<<gridn(pc->n), kT, 0, s>>>(x, pc->y64, pc->p, pc->z, pc->y,
+                                               op->mesh->d_dirichlet, pc->N, pc->n);
   FEM_CHECK_LAUNCH();
   if (!pc->exec || pc->g_b != b || pc->g_x != x || pc->gamma_built != pc->gamma) {
     FEM_CUDA_TRY(cudaStreamSynchronize(s));

@@ -149,10 +149,11 @@ def test_fcg_jacobi_only_converges_like_pcg():
     st = pc.fcg(b, x, rtol=1e-10)
     assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10
     x2 = torch.zeros_like(b)
-    st2 = op.solve_refined(b, x2, rtol=1e-10, inner_rtol=1e-5)
-    # FCG restarts its direction at each FP64 residual replacement, the refined
-    # PCG keeps it (reliable update): FCG needs more iterations, within 2x
-    assert st2["iterations"] <= st["iterations"] <= 2 * st2["iterations"] + 3
+    st2 = op.solve_refined(b, x2, rtol=1e-10, inner_rtol=0.1)
+    # with a fixed SPD preconditioner flexible CG is CG in exact arithmetic,
+    # and both keep their direction across the FP64 residual replacements:
+    # the counts differ only by FP32 rounding (beta formulas differ)
+    assert abs(st["iterations"] - st2["iterations"]) <= max(8, 0.2 * st2["iterations"])
     assert rel(x.cpu().numpy(), x2.cpu().numpy()) <= 1e-8
 
 
