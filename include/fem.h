@@ -384,6 +384,65 @@ fem_status fem_batch_autotune(fem_batch *batch, const double *const *b,
  * previous fem_batch_solve (it reuses the bound vectors). */
 fem_status fem_batch_barrier_selftest(fem_batch *batch, double timeout_ms);
 
+/* ---------------------------------------------------------------- p-multigrid */
+/* p-multigrid preconditioner (section "Ecosystem": multigrid on a hierarchy
+ * of polynomial degrees of one mesh, with matrix-free smoothers) and flexible
+ * CG around it.  The paper fixes no details; this library's choices:
+ *  - levels[0] is the finest operator, levels[nlevels-1] the coarsest; all
+ *    on meshes of the same elements in the same order (Gauss-Lobatto nodes,
+ *    element-local node order a + P b + P^2 c), with the kind, ncomp and
+ *    stream of level 0 and strictly decreasing orders; each level is its own
+ *    discretization (its own quadrature).  The hierarchy does not own them.
+ *  - prolongation level l+1 -> l: coarse element values interpolated at the
+ *    fine element's nodes (1D coarse Lagrange basis per direction), averaged
+ *    on shared nodes (weight 1 / multiplicity); restriction = its transpose;
+ *    both act on Dirichlet-masked vectors (zero on the levels' boundary).
+ *  - smoother: cheb_degree steps of the Chebyshev iteration (Saad 2003,
+ *    Alg. 12.1) on D^-1 A over [cheb_lo, cheb_hi] * lmax; lmax of each
+ *    smoothed level from power_its power iterations (FP64, at create) from
+ *    the SplitMix64 vector u_i = (splitmix64_i(seed 0) >> 11) 2^-53 - 1/2,
+ *    with the Rayleigh quotient v^T A v / v^T D v.
+ *  - coarsest level: coarse_its Jacobi-PCG iterations from zero.
+ *  - V-cycle: z = S(r); z += P V(R(r - A z)); z += S(r - A z), in FP64 or,
+ *    with prec = FEM_F32, on the levels' FP32 operators and vectors with
+ *    FP64 dot products (the levels must then be created with FEM_F32).
+ * Vectors are device [ncomp*N] FP64 of the level they belong to. */
+typedef struct fem_pmg fem_pmg;
+typedef struct {
+  int cheb_degree;    /* Chebyshev steps per smoothing, >= 1 (default 4) */
+  double cheb_lo;     /* smoothing interval [cheb_lo, cheb_hi] * lmax */
+  double cheb_hi;     /*   (defaults 0.1 and 1.1) */
+  int power_its;      /* power iterations for lmax, >= 1 (default 20) */
+  int coarse_its;     /* coarsest-level Jacobi-PCG iterations, >= 1 (30) */
+  int prec;           /* FEM_F64 or FEM_F32: precision of the V-cycle */
+} fem_pmg_opts;
+
+/* opts may be NULL (the defaults).  FEM_EINVAL for an inconsistent
+ * hierarchy, FEM_ENOMEM, FEM_EBREAKDOWN if a power iteration degenerates.
+ * Synchronizes the levels' stream. */
+fem_status fem_pmg_create(fem_op *const *levels, int nlevels, const fem_pmg_opts *opts,
+                          fem_pmg **out);
+fem_status fem_pmg_destroy(fem_pmg *pmg);
+/* lmax of a level (0 for the coarsest, which is not smoothed). */
+fem_status fem_pmg_get_lmax(const fem_pmg *pmg, int level, double *lmax);
+/* Override lmax of a smoothed level (lmax > 0). */
+fem_status fem_pmg_set_lmax(fem_pmg *pmg, int level, double lmax);
+/* xf = P xc, level+1 -> level (xf overwritten); FP64. */
+fem_status fem_pmg_prolong(fem_pmg *pmg, int level, const double *xc, double *xf);
+/* rc = R rf, level -> level+1 (rc overwritten); FP64. */
+fem_status fem_pmg_restrict(fem_pmg *pmg, int level, const double *rf, double *rc);
+/* z = B r, one V-cycle (r, z: level 0, FP64; r is only read).  The V-cycle
+ * is one CUDA graph, captured at the first call. */
+fem_status fem_pmg_vcycle(fem_pmg *pmg, const double *r, double *z);
+/* Flexible CG (Notay 2000, one stored direction) in FP64 on the constrained
+ * level-0 system with z = B r; x is the initial guess (its Dirichlet entries
+ * are kept).  opts: rtol (on the recursive residual, ||r|| <= rtol ||b||)
+ * and maxit; the rest is ignored.  One CUDA graph with a conditional WHILE
+ * node; synchronizes.  stats: iterations, rnorm, bnorm, true_rel = rnorm /
+ * bnorm.  FEM_OK, FEM_ENOCONV or FEM_EBREAKDOWN. */
+fem_status fem_pmg_solve(fem_pmg *pmg, const double *b, double *x, const fem_cg_opts *opts,
+                         fem_cg_stats *stats);
+
 /* ------------------------------------------------------- allocation-free solve */
 
 /* Largest ncomp*N accepted by fem_cg_solve_noalloc. */

@@ -59,6 +59,12 @@ _VP = ctypes.c_void_p
 _I64 = ctypes.c_int64
 
 
+class _PmgOpts(ctypes.Structure):
+    _fields_ = [("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("power_its", ctypes.c_int),
+                ("coarse_its", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
 def lib():
     """Load libfem.so.  Raises if the CUDA library has not been built."""
     global _lib
@@ -115,6 +121,15 @@ def lib():
         "fem_batch_autotune": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
                                ctypes.POINTER(_TuneResult)],
         "fem_batch_barrier_selftest": [_VP, ctypes.c_double],
+        "fem_pmg_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_PmgOpts),
+                           ctypes.POINTER(_VP)],
+        "fem_pmg_destroy": [_VP],
+        "fem_pmg_get_lmax": [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+        "fem_pmg_set_lmax": [_VP, ctypes.c_int, ctypes.c_double],
+        "fem_pmg_prolong": [_VP, ctypes.c_int, _VP, _VP],
+        "fem_pmg_restrict": [_VP, ctypes.c_int, _VP, _VP],
+        "fem_pmg_vcycle": [_VP, _VP, _VP],
+        "fem_pmg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -488,3 +503,59 @@ class Precond:
             _check(rc)
         return _stats(st)
 
+
+class Pmg:
+    """p-multigrid hierarchy over operators of decreasing order on the same
+    elements (include/fem.h, fem_pmg_*): Chebyshev-Jacobi smoothing,
+    interpolation transfers, Jacobi-PCG on the coarsest level; flexible CG
+    around one V-cycle per iteration.  `levels` finest first; the operators
+    must outlive this object."""
+
+    def __init__(self, levels, cheb_degree=4, cheb_lo=0.1, cheb_hi=1.1, power_its=20,
+                 coarse_its=30, prec=F64):
+        self.levels = list(levels)
+        arr = (_VP * len(self.levels))(*[o._h for o in self.levels])
+        o = _PmgOpts(int(cheb_degree), float(cheb_lo), float(cheb_hi), int(power_its),
+                     int(coarse_its), int(prec))
+        h = _VP()
+        _check(lib().fem_pmg_create(arr, len(self.levels), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.fem_pmg_destroy(self._h)
+            self._h = None
+
+    def lmax(self, level):
+        v = ctypes.c_double()
+        _check(lib().fem_pmg_get_lmax(self._h, int(level), ctypes.byref(v)))
+        return v.value
+
+    def set_lmax(self, level, value):
+        _check(lib().fem_pmg_set_lmax(self._h, int(level), float(value)))
+
+    def prolong(self, level, xc):
+        import torch
+        xf = torch.empty(self.levels[level].n, dtype=torch.float64, device=xc.device)
+        _check(lib().fem_pmg_prolong(self._h, int(level), _ptr(xc), _ptr(xf)))
+        return xf
+
+    def restrict(self, level, rf):
+        import torch
+        rc = torch.empty(self.levels[level + 1].n, dtype=torch.float64, device=rf.device)
+        _check(lib().fem_pmg_restrict(self._h, int(level), _ptr(rf), _ptr(rc)))
+        return rc
+
+    def vcycle(self, r):
+        import torch
+        z = torch.empty_like(r)
+        _check(lib().fem_pmg_vcycle(self._h, _ptr(r), _ptr(z)))
+        return z
+
+    def solve(self, b, x, rtol=1e-10, maxit=1000):
+        o = _CgOpts(0, int(maxit), float(rtol), 1, 0.0, 0)
+        st = _CgStats()
+        rc = lib().fem_pmg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        if rc not in (0, 5):
+            _check(rc)
+        return _stats(st)

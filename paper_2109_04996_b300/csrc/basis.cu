@@ -160,6 +160,18 @@ int fem_build_tables(int p, int q, int quad, BasisTables *t) {
   return FEM_OK;
 }
 
+// I[k][a] = l_a(x_k): the Lagrange basis of order p on its Gauss-Lobatto
+// nodes at npts points x (p-multigrid transfers).
+int fem_basis_interp(int p, const double *x, int npts, double *I) {
+  if (p < 1 || p + 1 > FEM_MAX_P) return FEM_EINVAL;
+  const int P = p + 1;
+  double z[FEM_MAX_P], zw[FEM_MAX_P], bw[FEM_MAX_P];
+  gauss_lobatto(P, z, zw);
+  bary_weights(P, z, bw);
+  for (int k = 0; k < npts; k++) bary_values(P, z, bw, x[k], I + k * P);
+  return FEM_OK;
+}
+
 extern "C" fem_status fem_basis_tables(int p, int q, int quad, double *nodes,
                                        double *qpts, double *qwts,
                                        double *interp, double *grad) {

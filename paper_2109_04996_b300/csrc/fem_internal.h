@@ -44,6 +44,8 @@ struct BasisTables {
                                           // on the quadrature points, at them
 };
 int fem_build_tables(int p, int q, int quad, BasisTables *t);
+// I[k][a] = l_a(x_k), Lagrange basis of order p on its Gauss-Lobatto nodes
+int fem_basis_interp(int p, const double *x, int npts, double *I);
 
 // Scalars of one CG run, resident on the device.
 struct CgScalars {

@@ -82,3 +82,14 @@ def test_mesh_create_rejects_bad_input_without_a_gpu(L):
     assert rc == 1 and b"out of" in L.fem_last_error()
     rc = L.fem_op_create(None, 1, 0, 4, 1, 0, None, 0, 1.0, ctypes.byref(h))
     assert rc == 1
+
+
+def test_pmg_create_rejects_bad_hierarchies_without_a_gpu(L):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.fem_pmg_create(arr, 0, None, ctypes.byref(h)) == 1
+    assert L.fem_pmg_create(arr, 9, None, ctypes.byref(h)) == 1
+    assert L.fem_pmg_create(arr, 2, None, ctypes.byref(h)) == 1
+    assert b"level 0" in L.fem_last_error()
+    assert L.fem_pmg_vcycle(None, None, None) == 1
+    assert L.fem_pmg_solve(None, None, None, None, None) == 1
