@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--learned-n", type=int, default=64, help="elements per direction, kappa BP3 p=4")
     ap.add_argument("--profile", default=None,
                     help="only time the apply of one operator, e.g. BP5:7:f32 (problem:order:prec)"
-                         " on a mesh of --dofs nodes; for profilers")
+                         " on a mesh of --dofs nodes, or PMG:4:f32 for p-multigrid V-cycles;"
+                         " for profilers")
     return ap.parse_args()
 
 
@@ -223,18 +224,33 @@ def run_reference(args):
 
 def time_to_solution(fem, torch, args):
     """BP3 at one order: wall time to ||b - A x|| <= 1e-10 ||b|| (true FP64
-    residual) for plain FP64 Jacobi-PCG and for FP32 inner PCG + FP64
-    iterative refinement, same mesh, same right-hand side, same GPU."""
+    residual) for plain FP64 Jacobi-PCG, for FP32 inner PCG + FP64 iterative
+    refinement, and for flexible CG with a p-multigrid V-cycle (orders p,
+    p/2, ..., 1 on the same elements; V-cycle in FP64 or FP32), same mesh,
+    same right-hand side, same GPU.  The multigrid set-up (coarse operators,
+    lmax estimates) is timed separately."""
     p = args.tts_order
     n = fem_inputs.bp3_mesh_n(args.tts_dofs, p)
-    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=300 + p)
+    orders = [p]
+    while orders[-1] > 1:
+        orders.append(max(1, orders[-1] // 2))
+    meshes = [fem_inputs.box_mesh(n, q, perturb=0.1, seed=300 + p) for q in orders]
+    m = meshes[0]
     gm = fem.Mesh(m)
     op = fem.Operator.bake_off(gm, "BP3", prec=fem.F32)
     b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=400 + p)).cuda()
-    out = {"problem": "BP3 p=%d n=%d N=%d" % (p, n, m["N"]), "rtol": 1e-10}
-    del m
+    out = {"problem": "BP3 p=%d n=%d N=%d" % (p, n, m["N"]), "rtol": 1e-10,
+           "pmg_orders": orders}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    coarse = [fem.Operator.bake_off(fem.Mesh(mm), "BP3", prec=fem.F32) for mm in meshes[1:]]
+    pmg = {"fp64_pmg_fcg": fem.Pmg([op] + coarse, prec=fem.F64),
+           "fp32_pmg_fcg": fem.Pmg([op] + coarse, prec=fem.F32)}
+    torch.cuda.synchronize()
+    out["pmg_setup_seconds"] = time.perf_counter() - t0
+    del meshes, m
     res = {}
-    for name in ("fp64_pcg", "fp32_refined"):
+    for name in ("fp64_pcg", "fp32_refined", "fp64_pmg_fcg", "fp32_pmg_fcg"):
         best = None
         for rep in range(2):  # first run builds the graphs
             x = torch.zeros_like(b)
@@ -242,8 +258,10 @@ def time_to_solution(fem, torch, args):
             t0 = time.perf_counter()
             if name == "fp64_pcg":
                 st = op.cg(b, x, precond=fem.PC_JACOBI, rtol=1e-10, maxit=100000)
-            else:
+            elif name == "fp32_refined":
                 st = op.solve_refined(b, x, rtol=1e-10, inner_rtol=0.1)
+            else:
+                st = pmg[name].solve(b, x, rtol=1e-10)
             torch.cuda.synchronize()
             t = time.perf_counter() - t0
             best = t if best is None else min(best, t)
@@ -255,6 +273,7 @@ def time_to_solution(fem, torch, args):
         res[name] = {"seconds": best, "iterations": st["iterations"], "outer": st["outer"],
                      "status": st["status"], "true_rel_residual": true_rel}
     res["speedup_refined_vs_fp64"] = res["fp64_pcg"]["seconds"] / res["fp32_refined"]["seconds"]
+    res["speedup_fp32_pmg_vs_fp64"] = res["fp64_pcg"]["seconds"] / res["fp32_pmg_fcg"]["seconds"]
     out.update(res)
     return out
 
@@ -482,6 +501,29 @@ def run_profile(args):
     name, p, prec = args.profile.split(":")
     p = int(p)
     n = fem_inputs.bp3_mesh_n(args.dofs, p)
+    if name == "PMG":
+        # one p-multigrid V-cycle (BP3 levels p, p/2, ..., 1) per step
+        orders = [p]
+        while orders[-1] > 1:
+            orders.append(max(1, orders[-1] // 2))
+        meshes = [fem_inputs.box_mesh(n, q, perturb=0.1, seed=900) for q in orders]
+        ops = [fem.Operator.bake_off(fem.Mesh(mm), "BP3", prec=fem.F32) for mm in meshes]
+        pm = fem.Pmg(ops, prec=fem.F32 if prec == "f32" else fem.F64)
+        N = meshes[0]["N"]
+        r = torch.from_numpy(np.where(meshes[0]["dirichlet"] == 0,
+                                      np.random.default_rng(0).uniform(-1, 1, N), 0.0)).cuda()
+        for _ in range(args.warmup):
+            pm.vcycle(r)
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(args.steps):
+            pm.vcycle(r)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        print(json.dumps({"profile": args.profile, "N": N, "E": meshes[0]["E"], "n": n,
+                          "orders": orders, "ms_per_vcycle": ms}))
+        return
     m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=900)
     gm = fem.Mesh(m)
     op = fem.Operator.bake_off(gm, name, prec=fem.F32)
