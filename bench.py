@@ -48,9 +48,11 @@ def parse():
     ap.add_argument("--tts-dofs", type=float, default=1e7,
                     help="size of the time-to-1e-10 comparison (0 = skip)")
     ap.add_argument("--tts-order", type=int, default=4)
-    ap.add_argument("--sections", default="bp56,batched,learned",
-                    help="extra measured configurations: bp56, batched, learned (comma list)")
+    ap.add_argument("--sections", default="bp56,suite,batched,learned",
+                    help="extra measured configurations: bp56, suite, batched, learned (comma list)")
     ap.add_argument("--bp56-n", type=int, default=44, help="elements per direction, BP5/BP6 p=7")
+    ap.add_argument("--suite-order", type=int, default=4, help="order of the BP1-BP6 suite section")
+    ap.add_argument("--suite-dofs", type=float, default=8e6, help="nodes of the BP1-BP6 suite mesh")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--learned-n", type=int, default=64, help="elements per direction, kappa BP3 p=4")
     ap.add_argument("--profile", default=None,
@@ -354,6 +356,53 @@ def section_bp56(fem, torch, args):
             "time_to_1e-10": tts,
             "speedup_refined_vs_fp64": tts["fp64_pcg"]["seconds"] / tts["fp32_refined"]["seconds"]}
         del op, x, y, x32, y32, b
+    return out
+
+
+def section_suite(fem, torch, args):
+    """All six bake-off problems (BP1/BP2 mass, BP3/BP4 diffusion with Gauss
+    q = p+2, BP5/BP6 diffusion on the Gauss-Lobatto points; odd = scalar,
+    even = 3 components) on one mesh at one order: FP64 and FP32 apply
+    throughput and the FP64 CG iteration rate (graph-captured, 20 iterations;
+    no preconditioner for the mass problems, Jacobi for the others)."""
+    p = args.suite_order
+    n = fem_inputs.bp3_mesh_n(args.suite_dofs, p)
+    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=700)
+    gm = fem.Mesh(m)
+    N, E = m["N"], m["E"]
+    hbm = measured_peaks().get("hbm_gbs", 6400.0)
+    out = {"mesh": "p=%d n=%d N=%d nodes" % (p, n, N)}
+    iters = 20
+    for name in ("BP1", "BP2", "BP3", "BP4", "BP5", "BP6"):
+        kind, nc, quad, dq = fem.BAKE_OFF[name]
+        op = fem.Operator.bake_off(gm, name, prec=fem.F32)
+        P, q = p + 1, p + dq
+        nd = 1 if kind == fem.MASS else 6
+        x = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, nc * N)).cuda()
+        y = torch.empty_like(x)
+        x32, y32 = x.float(), torch.empty(nc * N, dtype=torch.float32, device="cuda")
+        t64 = _time_apply(torch, lambda: op.apply(x, y))
+        t32 = _time_apply(torch, lambda: op.apply_f32(x32, y32))
+        by64 = nc * 16 * N + 4 * E * P ** 3 + 8 * nd * E * q ** 3
+        by32 = nc * 8 * N + 4 * E * P ** 3 + 4 * nd * E * q ** 3
+        b = torch.from_numpy(fem_inputs.rhs_uniform(N, m["dirichlet"], seed=701, ncomp=nc)).cuda()
+        pc = fem.PC_NONE if kind == fem.MASS else fem.PC_JACOBI
+        xs = torch.zeros_like(b)
+        op.cg(b, xs, precond=pc, maxit=iters, rtol=0.0)   # builds the graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs.zero_()
+        st = op.cg(b, xs, precond=pc, maxit=iters, rtol=0.0)
+        torch.cuda.synchronize()
+        tcg = time.perf_counter() - t0
+        out[name] = {"dofs": nc * N, "q": q,
+                     "apply_f64": {"ms": t64 * 1e3, "gdofs": nc * N / t64 / 1e9,
+                                   "hbm_gbs": by64 / t64 / 1e9},
+                     "apply_f32": {"ms": t32 * 1e3, "gdofs": nc * N / t32 / 1e9,
+                                   "hbm_gbs": by32 / t32 / 1e9,
+                                   "hbm_frac_of_measured": by32 / t32 / 1e9 / hbm},
+                     "cg_f64_gdofs_per_iteration": nc * N * st["iterations"] / tcg / 1e9}
+        del op, x, y, x32, y32, b, xs
     return out
 
 
@@ -683,6 +732,8 @@ def main():
     secs = [t for t in args.sections.split(",") if t]
     if "bp56" in secs:
         line["bp5_bp6"] = section_bp56(fem, torch, args)
+    if "suite" in secs:
+        line["bp_suite"] = section_suite(fem, torch, args)
     if "batched" in secs:
         line["batched"] = section_batched(fem, torch, args)
     if "learned" in secs:

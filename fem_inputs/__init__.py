@@ -85,6 +85,41 @@ def box_mesh(n, p, perturb=0.1, seed=0, shuffle_seed=None):
                 dirichlet=dirichlet, perm=perm, n=n, p=p, N=N, E=E, M=M)
 
 
+def cube_rotations():
+    """The 24 proper rotations of the cube as 3x3 signed permutation matrices
+    (det +1)."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3), dtype=np.int64)
+            for r, c in enumerate(perm):
+                R[r, c] = signs[r]
+            if round(np.linalg.det(R)) == 1:
+                out.append(R)
+    return out
+
+
+def rotate_elements(mesh, seed):
+    """The same mesh with each element's local frame turned by a seeded
+    proper rotation of the cube: elem_verts [E, 8] are permuted so that new
+    local vertex c' (c' in {0,1}^3, index i + 2j + 4k) is the old vertex at
+    (R (2c' - 1) + 1) / 2.  elem_nodes and dirichlet are dropped (they must be
+    rebuilt from the vertices); vertex coordinates are unchanged."""
+    rots = cube_rotations()
+    choice = _rng(seed).integers(0, len(rots), size=mesh["E"])
+    corners = np.array([[v & 1, (v >> 1) & 1, (v >> 2) & 1] for v in range(8)], dtype=np.int64)
+    maps = []
+    for R in rots:
+        old = ((R @ (2 * corners.T - 1)) + 1) // 2            # [3, 8]
+        maps.append(old[0] + 2 * old[1] + 4 * old[2])
+    maps = np.array(maps)                                      # [24, 8]
+    ev = mesh["elem_verts"]
+    new_ev = np.take_along_axis(ev, maps[choice], axis=1).astype(np.int32)
+    return dict(vert_xyz=mesh["vert_xyz"], elem_verts=np.ascontiguousarray(new_ev), p=mesh["p"],
+                E=mesh["E"], n=mesh.get("n"))
+
+
 def elements_of_nodes(mesh, rows):
     """CSR list of the elements that contain each global node in `rows`.
 

@@ -118,6 +118,19 @@ fem_status fem_mesh_create_vertices(int p, int64_t N, int64_t E,
                                     const int32_t *elem_verts_host,
                                     const uint8_t *dirichlet_host, void *stream,
                                     fem_mesh **out);
+/* Q_p connectivity of an unstructured hexahedral mesh given by its
+ * elements' vertices (host, no GPU): elem_verts_host [E][8] in local order
+ * i + 2j + 4k (any orientation per element, right-handed); the element-node
+ * table [E][(p+1)^3] (local a + P b + P^2 c) is written with one global id per
+ * node of the C^0 Q_p space: vertices, then edge nodes ordered from the
+ * edge's lower vertex id, face nodes in a frame anchored at the face's lowest
+ * vertex id, interior nodes; ids in order of first use.  dirichlet_host (may
+ * be NULL; room for E*(p+1)^3 bytes) gets 1 on every node of a face that
+ * belongs to one element only.  *N_out = number of nodes.  FEM_EINVAL for
+ * vertex ids out of [0, nvert), an element repeating a vertex, a face of
+ * more than two elements, or more than 2^31-1 nodes. */
+fem_status fem_mesh_connectivity(int p, int64_t nvert, int64_t E, const int32_t *elem_verts_host,
+                                 int32_t *elem_nodes_host, uint8_t *dirichlet_host, int64_t *N_out);
 /* Node coordinates [N][3] of a mesh, copied to host (synchronizes). */
 fem_status fem_mesh_node_coords(const fem_mesh *mesh, double *xyz_host);
 fem_status fem_mesh_destroy(fem_mesh *mesh);

@@ -82,6 +82,8 @@ def lib():
         "fem_mesh_create_vertices": [ctypes.c_int, _I64, _I64, _VP, _I64, _VP, _VP, _VP, _VP,
                                      ctypes.POINTER(_VP)],
         "fem_mesh_node_coords": [_VP, _VP],
+        "fem_mesh_connectivity": [ctypes.c_int, _I64, _I64, _VP, _VP, _VP,
+                                  ctypes.POINTER(ctypes.c_int64)],
         "fem_op_create": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                           ctypes.c_int, _VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_VP)],
         "fem_op_destroy": [_VP],
@@ -167,6 +169,25 @@ def basis_tables(p, q, quad):
     out = [np.zeros(P), np.zeros(q), np.zeros(q), np.zeros((q, P)), np.zeros((q, P))]
     _check(lib().fem_basis_tables(p, q, quad, *[_ptr(a) for a in out]))
     return dict(nodes=out[0], qpts=out[1], qwts=out[2], interp=out[3], grad=out[4])
+
+
+def mesh_connectivity(p, vert_xyz, elem_verts):
+    """Q_p connectivity of a hexahedral mesh given by its vertices
+    (fem_mesh_connectivity, host): returns a mesh dict like
+    fem_inputs.box_mesh's (vert_xyz, elem_verts, elem_nodes, dirichlet, n=None,
+    p, N, E), with Dirichlet nodes on the faces of one element only."""
+    ev = np.ascontiguousarray(elem_verts, dtype=np.int32)
+    vx = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+    E = ev.shape[0]
+    P = p + 1
+    en = np.empty((E, P ** 3), dtype=np.int32)
+    dr = np.empty(E * P ** 3, dtype=np.uint8)
+    N = ctypes.c_int64()
+    _check(lib().fem_mesh_connectivity(int(p), vx.shape[0], E, ev.ctypes.data, en.ctypes.data,
+                                       dr.ctypes.data, ctypes.byref(N)))
+    N = N.value
+    return dict(vert_xyz=vx, elem_verts=ev, elem_nodes=en, dirichlet=dr[:N].copy(), n=None,
+                p=int(p), N=N, E=E, M=None, perm=np.arange(E, dtype=np.int64))
 
 
 def nodes_from_vertices(mesh):
