@@ -45,6 +45,29 @@ int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
 }
 
 // Diffusion: the line-based, even-odd element body (apply_lines.cuh).
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE>
+int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
+  constexpr int NT = ApplyShape<Q, EPB>::NT;
+  constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
+  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE>;
+  static int max_bps = -1;
+  if (max_bps < 0) {
+    FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+    max_bps = per_sm < 1 ? 1 : per_sm;
+  }
+  const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
+  const int64_t ngroups = (lp.a.nsel + EPB - 1) / EPB;
+  int64_t grid = (int64_t)op->nsm * use;
+  if (grid > ngroups) grid = ngroups;
+  if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, NT, smem, op->stream()>>>(lp);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
 template <typename T, int P, int Q, bool COLLOC, int EPB>
 int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
@@ -64,23 +87,11 @@ int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
     make_symtab<T, Q, P>(Bt, lp.t.Bt);
     make_symtab<T, Q, Q>(op->tab.Dq, lp.t.Df);
     make_symtab<T, Q, Q>(Dt, lp.t.Dt);
-    auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB>;
-    static int max_bps = -1;
-    if (max_bps < 0) {
-      FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      int per_sm = 0;
-      FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-      max_bps = per_sm < 1 ? 1 : per_sm;
+    if constexpr (sizeof(T) == 4) {
+      if (prm.ncomp == 1 && !prm.list)
+        return launch_lines_kernel<T, P, Q, COLLOC, EPB, true>(op, lp, bps);
     }
-    const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
-    const int64_t ngroups = (prm.nsel + EPB - 1) / EPB;
-    int64_t grid = (int64_t)op->nsm * use;
-    if (grid > ngroups) grid = ngroups;
-    if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
-    if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, NT, smem, op->stream()>>>(lp);
-    FEM_CHECK_LAUNCH();
-    return FEM_OK;
+    return launch_lines_kernel<T, P, Q, COLLOC, EPB, false>(op, lp, bps);
   }
 }
 

@@ -120,10 +120,45 @@ constexpr size_t lines_smem_bytes() {
   return sizeof(T) * (size_t)EPB * 4 * LineCube<Q>::size;
 }
 
-template <typename T, int P, int Q, bool COLLOC, int EPB>
+// One thread's z-column of an element: its P node ids and gathered values.
+// The pipelined loop carries the next group's column across iterations so
+// that its loads overlap the current group's stages.
+template <typename T, int P>
+struct Column {
+  int32_t idx[P];
+  T u[P];
+};
+
+// Column of element group g for the calling thread (a P x P line set
+// thread); zeros where the element does not exist.
+template <typename T, int P, int Q, int EPB>
+__device__ __forceinline__ void column_indices(const ApplyParams<T> &prm, int64_t g, Column<T, P> &col) {
+  constexpr int Q2 = Q * Q, P2 = P * P, P3 = P * P * P;
+  const int slot_raw = threadIdx.x / Q2, t = threadIdx.x - slot_raw * Q2;
+  const int64_t k_el = g * EPB + slot_raw;
+  const bool ok = slot_raw < EPB && t < P2 && k_el < prm.nsel;
+  const int32_t *en = prm.elem_nodes + (ok ? k_el : 0) * P3 + (t % P) + P * (t / P);
+#pragma unroll
+  for (int k = 0; k < P; k++) col.idx[k] = ok ? en[P2 * k] : -1;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void column_values(const ApplyParams<T> &prm, Column<T, P> &col) {
+#pragma unroll
+  for (int k = 0; k < P; k++)
+    col.u[k] = col.idx[k] >= 0 ? gather_load(&prm.x[col.idx[k]], prm.x_l2_only) : T(0);
+}
+
+// PIPE (scalar operator, contiguous elements): the column of this group is
+// given in `cur` (ids and values loaded by the previous iteration) and the
+// next group's (g + gridDim.x) is loaded into `nxt`: its ids at the start,
+// its values after the gradient stage.
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE = false>
 __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
                                                   const LineTables<T, P, Q> &tb, int64_t g,
-                                                  T *cubes, double &dot) {
+                                                  T *cubes, double &dot,
+                                                  const Column<T, P> *cur = nullptr,
+                                                  Column<T, P> *nxt = nullptr) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P2 = P * P, P3 = P * P * P;
   constexpr int CS = LineCube<Q>::size;
   // cube entry (k, j, i) (see LineCube for the pitch)
@@ -150,14 +185,20 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   // this thread's share of x.y over the group (see DotAcc), added to the
   // FP64 `dot` once
   DotAcc<T> dl;
+  if constexpr (PIPE) column_indices<T, P, Q, EPB>(prm, g + gridDim.x, *nxt);
   for (int c = 0; c < prm.ncomp; c++) {
     const T *xc = prm.x + c * N;
     T *yc = prm.y + c * N;
     // ---- gather the z-column (a, b) = (lp0, lp1) of the element
     T u[P];
+    if constexpr (PIPE) {
 #pragma unroll
-    for (int k = 0; k < P; k++)
-      u[k] = (valid && on_pp) ? gather_load(&xc[en[lp0 + P * lp1 + P2 * k]], prm.x_l2_only) : T(0);
+      for (int k = 0; k < P; k++) u[k] = cur->u[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < P; k++)
+        u[k] = (valid && on_pp) ? gather_load(&xc[en[lp0 + P * lp1 + P2 * k]], prm.x_l2_only) : T(0);
+    }
     // c3 holds the values at the quadrature points, x-contiguous [k][j][i]
     if constexpr (COLLOC) {
       if (on_pp) {
@@ -217,6 +258,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       for (int m = 0; m < Q; m++) c4[ix(m, lq1, lq0)] = out[m];
     }
     __syncthreads();
+    if constexpr (PIPE) column_values<T, P>(prm, *nxt);
     // ---- pointwise D at the column (iq, jq) = (lq0, lq1), in place
     if (on_qq) {
 #pragma unroll
@@ -263,7 +305,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
           const int pt = ix(k, lp1, lp0);
           const T s = c1[pt] + c2[pt] + c4[pt];
           if (valid) {
-            const int64_t gi = en[lp0 + P * lp1 + P2 * k];
+            const int64_t gi = PIPE ? cur->idx[k] : en[lp0 + P * lp1 + P2 * k];
             atomic_add(&yc[gi], s);
             dl.add(s, u[k]);
           }
@@ -305,7 +347,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
 #pragma unroll
         for (int k = 0; k < P; k++) {
           if (valid) {
-            const int64_t gi = en[lp0 + P * lp1 + P2 * k];
+            const int64_t gi = PIPE ? cur->idx[k] : en[lp0 + P * lp1 + P2 * k];
             atomic_add(&yc[gi], out[k]);
             dl.add(out[k], u[k]);
           }
@@ -318,7 +360,11 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   if (prm.dot_out || prm.want_dot) dot += dl.get();
 }
 
-template <typename T, int P, int Q, bool COLLOC, int EPB>
+// PIPE: the group loop carries each group's column gather one group ahead
+// (scalar operators over contiguous elements; the launcher picks it for FP32,
+// whose time is load latency); a separate instantiation, so that the others
+// keep their lower register count.
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE>
 __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     fem_apply_lines_kernel(const LineParams<T, P, Q> lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -326,8 +372,18 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
   const ApplyParams<T> &prm = lp.a;
   double dot = 0.0;
   const int64_t ngroups = (prm.nsel + EPB - 1) / EPB;
-  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
-    apply_group_lines<T, P, Q, COLLOC, EPB>(prm, lp.t, g, cubes, dot);
+  if constexpr (PIPE) {
+    Column<T, P> cur, nxt;
+    column_indices<T, P, Q, EPB>(prm, blockIdx.x, cur);
+    column_values<T, P>(prm, cur);
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+      apply_group_lines<T, P, Q, COLLOC, EPB, true>(prm, lp.t, g, cubes, dot, &cur, &nxt);
+      cur = nxt;
+    }
+  } else {
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
+      apply_group_lines<T, P, Q, COLLOC, EPB>(prm, lp.t, g, cubes, dot);
+  }
   if (prm.dot_out) {
     double v[1] = {dot};
     __shared__ double tot[1];
