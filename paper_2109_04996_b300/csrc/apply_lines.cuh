@@ -108,16 +108,26 @@ inline void make_symtab(const double *M, SymTab<T, NI, NO> &s) {
 // through shared memory by the pitch, and a pitch of 4 or 8 words would put
 // 4 or 8 of a warp's threads on one bank (measured: BP5/BP6 p=7 +3-15 %);
 // for q = 6 or 10 (2-way) the extra space costs more occupancy than it saves.
-template <int Q>
+// PAD = false keeps the pitch q (the batched kernel, which holds every order
+// in one kernel and is register-bound).
+template <int Q, bool PAD = true>
 struct LineCube {
-  static constexpr int pitch = (Q % 4 == 0) ? Q + 1 : Q;
+  static constexpr int pitch = (PAD && Q % 4 == 0) ? Q + 1 : Q;
   static constexpr int size = Q * Q * pitch;
 };
 
+// Index of cube entry (k, j, i).  (A function, not a lambda: with a lambda
+// here the batched kernel, which inlines every order, took 119 registers
+// instead of 72.)
+template <int Q, int PITCH>
+__device__ __forceinline__ int cube_ix(int k, int j, int i) {
+  return (k * Q + j) * PITCH + i;
+}
+
 // Shared memory: 4 cubes per element slot.
-template <typename T, int Q, int EPB>
+template <typename T, int Q, int EPB, bool PAD = true>
 constexpr size_t lines_smem_bytes() {
-  return sizeof(T) * (size_t)EPB * 4 * LineCube<Q>::size;
+  return sizeof(T) * (size_t)EPB * 4 * LineCube<Q, PAD>::size;
 }
 
 // One thread's z-column of an element: its P node ids and gathered values.
@@ -153,16 +163,14 @@ __device__ __forceinline__ void column_values(const ApplyParams<T> &prm, Column<
 // given in `cur` (ids and values loaded by the previous iteration) and the
 // next group's (g + gridDim.x) is loaded into `nxt`: its ids at the start,
 // its values after the gradient stage.
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE = false>
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE = false, bool PAD = true>
 __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
                                                   const LineTables<T, P, Q> &tb, int64_t g,
                                                   T *cubes, double &dot,
                                                   const Column<T, P> *cur = nullptr,
                                                   Column<T, P> *nxt = nullptr) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P2 = P * P, P3 = P * P * P;
-  constexpr int CS = LineCube<Q>::size;
-  // cube entry (k, j, i) (see LineCube for the pitch)
-  auto ix = [](int k, int j, int i) { return (k * Q + j) * LineCube<Q>::pitch + i; };
+  constexpr int CS = LineCube<Q, PAD>::size, PITCH = LineCube<Q, PAD>::pitch;
   const int slot_raw = threadIdx.x / Q2;
   const bool live = slot_raw < EPB;
   const int slot = live ? slot_raw : EPB - 1;
@@ -203,7 +211,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
     if constexpr (COLLOC) {
       if (on_pp) {
 #pragma unroll
-        for (int k = 0; k < Q; k++) c3[ix(k, lp1, lp0)] = u[k];
+        for (int k = 0; k < Q; k++) c3[cube_ix<Q, PITCH>(k, lp1, lp0)] = u[k];
       }
     } else {
       // z-interpolation of the column (a, b)
@@ -211,27 +219,27 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T w[Q];
         sym_apply<+1>(tb.Bf, u, w);
 #pragma unroll
-        for (int k = 0; k < Q; k++) c1[ix(k, lp1, lp0)] = w[k];
+        for (int k = 0; k < Q; k++) c1[cube_ix<Q, PITCH>(k, lp1, lp0)] = w[k];
       }
       __syncthreads();
       // y-lines (a, kq): c1[kq][0..P)[a] -> c2[kq][0..Q)[a]
       if (on_pq) {
         T in[P], out[Q];
 #pragma unroll
-        for (int j = 0; j < P; j++) in[j] = c1[ix(lp1, j, lp0)];
+        for (int j = 0; j < P; j++) in[j] = c1[cube_ix<Q, PITCH>(lp1, j, lp0)];
         sym_apply<+1>(tb.Bf, in, out);
 #pragma unroll
-        for (int j = 0; j < Q; j++) c2[ix(lp1, j, lp0)] = out[j];
+        for (int j = 0; j < Q; j++) c2[cube_ix<Q, PITCH>(lp1, j, lp0)] = out[j];
       }
       __syncthreads();
       // x-lines (jq, kq): c2[kq][jq][0..P) -> c3[kq][jq][0..Q)
       if (on_qq) {
         T in[P], out[Q];
 #pragma unroll
-        for (int i = 0; i < P; i++) in[i] = c2[ix(lq1, lq0, i)];
+        for (int i = 0; i < P; i++) in[i] = c2[cube_ix<Q, PITCH>(lq1, lq0, i)];
         sym_apply<+1>(tb.Bf, in, out);
 #pragma unroll
-        for (int i = 0; i < Q; i++) c3[ix(lq1, lq0, i)] = out[i];
+        for (int i = 0; i < Q; i++) c3[cube_ix<Q, PITCH>(lq1, lq0, i)] = out[i];
       }
     }
     __syncthreads();
@@ -240,22 +248,22 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       T in[Q], out[Q];
       // x-line (jq, kq) = (lq0, lq1)
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c3[ix(lq1, lq0, m)];
+      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<Q, PITCH>(lq1, lq0, m)];
       sym_apply<-1>(tb.Df, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c1[ix(lq1, lq0, m)] = out[m];
+      for (int m = 0; m < Q; m++) c1[cube_ix<Q, PITCH>(lq1, lq0, m)] = out[m];
       // y-line (iq, kq) = (lq0, lq1)
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c3[ix(lq1, m, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<Q, PITCH>(lq1, m, lq0)];
       sym_apply<-1>(tb.Df, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c2[ix(lq1, m, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c2[cube_ix<Q, PITCH>(lq1, m, lq0)] = out[m];
       // z-line (iq, jq) = (lq0, lq1)
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c3[ix(m, lq1, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<Q, PITCH>(m, lq1, lq0)];
       sym_apply<-1>(tb.Df, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c4[ix(m, lq1, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c4[cube_ix<Q, PITCH>(m, lq1, lq0)] = out[m];
     }
     __syncthreads();
     if constexpr (PIPE) column_values<T, P>(prm, *nxt);
@@ -263,10 +271,11 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
     if (on_qq) {
 #pragma unroll
       for (int kq = 0; kq < Q; kq++) {
-        const int pt = ix(kq, lq1, lq0);
+        const int pt = cube_ix<Q, PITCH>(kq, lq1, lq0);
         T G00 = 0, G11 = 0, G22 = 0, G12 = 0, G02 = 0, G01 = 0;
         if (valid) {
-          const T *qk = qd + (kq * Q + lq1) * Q + lq0;   // qdata is unpadded
+          // qdata is unpadded: the cube index unless the cube is padded
+          const T *qk = qd + (LineCube<Q, PAD>::pitch == Q ? pt : (kq * Q + lq1) * Q + lq0);
           G00 = qk[0]; G11 = qk[Q3]; G22 = qk[2 * Q3];
           G12 = qk[3 * Q3]; G02 = qk[4 * Q3]; G01 = qk[5 * Q3];
         }
@@ -281,20 +290,20 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
     if (on_qq) {
       T in[Q], out[Q];
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c1[ix(lq1, lq0, m)];
+      for (int m = 0; m < Q; m++) in[m] = c1[cube_ix<Q, PITCH>(lq1, lq0, m)];
       sym_apply<-1>(tb.Dt, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c1[ix(lq1, lq0, m)] = out[m];
+      for (int m = 0; m < Q; m++) c1[cube_ix<Q, PITCH>(lq1, lq0, m)] = out[m];
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c2[ix(lq1, m, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c2[cube_ix<Q, PITCH>(lq1, m, lq0)];
       sym_apply<-1>(tb.Dt, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c2[ix(lq1, m, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c2[cube_ix<Q, PITCH>(lq1, m, lq0)] = out[m];
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c4[ix(m, lq1, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c4[cube_ix<Q, PITCH>(m, lq1, lq0)];
       sym_apply<-1>(tb.Dt, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c4[ix(m, lq1, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c4[cube_ix<Q, PITCH>(m, lq1, lq0)] = out[m];
     }
     __syncthreads();
     if constexpr (COLLOC) {
@@ -302,7 +311,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       if (on_pp) {
 #pragma unroll
         for (int k = 0; k < P; k++) {
-          const int pt = ix(k, lp1, lp0);
+          const int pt = cube_ix<Q, PITCH>(k, lp1, lp0);
           const T s = c1[pt] + c2[pt] + c4[pt];
           if (valid) {
             const int64_t gi = PIPE ? cur->idx[k] : en[lp0 + P * lp1 + P2 * k];
@@ -320,29 +329,29 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T in[Q], out[P];
 #pragma unroll
         for (int m = 0; m < Q; m++) {
-          const int pt = ix(lq1, lq0, m);
+          const int pt = cube_ix<Q, PITCH>(lq1, lq0, m);
           in[m] = c1[pt] + c2[pt] + c4[pt];
         }
         sym_apply<+1>(tb.Bt, in, out);
 #pragma unroll
-        for (int i = 0; i < P; i++) c3[ix(lq1, lq0, i)] = out[i];
+        for (int i = 0; i < P; i++) c3[cube_ix<Q, PITCH>(lq1, lq0, i)] = out[i];
       }
       __syncthreads();
       // y-lines (a, kq): c3[kq][0..Q)[a] -> c1[kq][0..P)[a]
       if (on_pq) {
         T in[Q], out[P];
 #pragma unroll
-        for (int j = 0; j < Q; j++) in[j] = c3[ix(lp1, j, lp0)];
+        for (int j = 0; j < Q; j++) in[j] = c3[cube_ix<Q, PITCH>(lp1, j, lp0)];
         sym_apply<+1>(tb.Bt, in, out);
 #pragma unroll
-        for (int j = 0; j < P; j++) c1[ix(lp1, j, lp0)] = out[j];
+        for (int j = 0; j < P; j++) c1[cube_ix<Q, PITCH>(lp1, j, lp0)] = out[j];
       }
       __syncthreads();
       // z-lines (a, b): c1[0..Q)[b][a] -> nodes, scatter
       if (on_pp) {
         T in[Q], out[P];
 #pragma unroll
-        for (int k = 0; k < Q; k++) in[k] = c1[ix(k, lp1, lp0)];
+        for (int k = 0; k < Q; k++) in[k] = c1[cube_ix<Q, PITCH>(k, lp1, lp0)];
         sym_apply<+1>(tb.Bt, in, out);
 #pragma unroll
         for (int k = 0; k < P; k++) {

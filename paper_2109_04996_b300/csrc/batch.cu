@@ -247,7 +247,7 @@ __device__ void batch_group_lines(const BatchProblem &pr, int64_t g, unsigned ch
   prm.partials = nullptr; prm.counter = nullptr; prm.dot_out = nullptr;
   prm.x_l2_only = 0;  // written before the last grid barrier (see grid_barrier)
   prm.want_dot = 1;   // p^T A p of the problem
-  apply_group_lines<float, P, Q, false, EPB>(prm, batch_ltab<P>(), g, cubes, dot);
+  apply_group_lines<float, P, Q, false, EPB, false, false>(prm, batch_ltab<P>(), g, cubes, dot);
 }
 
 template <int NT>
@@ -268,7 +268,7 @@ __device__ void batch_group_lines_p(const BatchProblem &pr, int64_t g, unsigned 
 template <int NT>
 constexpr size_t batch_lines_smem() {
   size_t m = 0;
-#define FEM_BL(P) { size_t s = fem_apply::lines_smem_bytes<float, P + 1, BatchEpb<NT, P + 1>::value>(); if (s > m) m = s; }
+#define FEM_BL(P) { size_t s = fem_apply::lines_smem_bytes<float, P + 1, BatchEpb<NT, P + 1>::value, false>(); if (s > m) m = s; }
   FEM_BL(2) FEM_BL(3) FEM_BL(4) FEM_BL(5) FEM_BL(6) FEM_BL(7) FEM_BL(8) FEM_BL(9)
 #undef FEM_BL
   return m;
