@@ -406,12 +406,11 @@ def section_suite(fem, torch, args):
     return out
 
 
-def section_batched(fem, torch, args):
-    """64 independent BP3 problems (n in 4..32, p in 2..8 from seed 7), FP32
-    operators with FP64 refinement, all inner iterations in one persistent
-    kernel per outer step, autotuned block shape; vs the same problems solved
-    one after another with fem_solve_refined."""
-    specs = fem_inputs.batch_problems(args.batch_count, seed=7)
+def _batched_mix(fem, torch, specs):
+    """One batch of independent BP3 problems: FP32 operators with FP64
+    refinement, all inner iterations in one persistent kernel per outer
+    step, autotuned block shape; vs the same problems solved one after
+    another with fem_solve_refined (graphs warmed first)."""
     probs = []
     for s_ in specs:
         m = fem_inputs.box_mesh(s_["n"], s_["p"], perturb=0.1, seed=s_["mesh_seed"])
@@ -449,10 +448,21 @@ def section_batched(fem, torch, args):
         seq += time.perf_counter() - t0
     return {"problems": len(probs), "total_dofs": sum(q[1].N for q in probs),
             "orders": sorted(set(s_["p"] for s_ in specs)),
+            "sizes_n": [min(s_["n"] for s_ in specs), max(s_["n"] for s_ in specs)],
             "seconds": best, "gdofs_per_cg_iteration": dof_it / best / 1e9,
             "max_true_rel_residual": worst, "all_converged": all(r["status"] == "FEM_OK" for r in res),
             "autotune": dict(tune, seconds=t_tune),
             "sequential_refined_seconds": seq, "speedup_vs_sequential": seq / best}
+
+
+def section_batched(fem, torch, args):
+    """Two batches: the bake-off mix (64 BP3 problems, n in 4..32, p in 2..8,
+    seed 7: total work dominated by a few large high-order problems) and a
+    small-problem mix (256 problems, n in 2..8, p in 1..4, seed 8: each
+    solve alone is bound by launch and iteration latency)."""
+    return {"bake_off_mix": _batched_mix(fem, torch, fem_inputs.batch_problems(args.batch_count, seed=7)),
+            "small_mix": _batched_mix(fem, torch, fem_inputs.batch_problems(
+                4 * args.batch_count, seed=8, nmin=2, nmax=8, pmin=1, pmax=4))}
 
 
 def section_learned(fem, torch, args):
