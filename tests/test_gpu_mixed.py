@@ -90,3 +90,15 @@ def test_refined_requires_f32_operator_and_limits_outer_steps():
     op = fem.Operator.bake_off(gm, "BP3", prec=fem.F32)
     st = op.solve_refined(b, torch.zeros_like(b), rtol=1e-14, inner_rtol=0.5, max_outer=2)
     assert st["status"] == "FEM_ENOCONV" and st["outer"] <= 3
+
+
+@pytest.mark.parametrize("name,p,n", [("BP3", 2, 14), ("BP3", 4, 11), ("BP5", 7, 9), ("BP3", 8, 6)])
+def test_pipelined_fp32_apply_over_many_groups_per_block(name, p, n):
+    # one block per SM: every block walks several element groups, so the
+    # FP32 kernel's next-group column loads are exercised, and E is not a
+    # multiple of the group size (ragged last group)
+    m, gm, op, orc = make(name, n, p, shuffle=11)
+    op.set_launch_shape(fem.F32, 0, 1)
+    x = np.random.default_rng(8).uniform(-1, 1, op.ncomp * m["N"])
+    y = op.apply_f32(torch.from_numpy(x).float().cuda()).double().cpu().numpy()
+    assert rel(y, orc.apply(x)) <= TOL32

@@ -132,3 +132,21 @@ def test_pmg_rejects_inconsistent_hierarchies():
         fem.Pmg([oa, oc])            # order not decreasing
     with pytest.raises(fem.FemError):
         fem.Pmg([oc, oa], prec=fem.F32)   # FP32 V-cycle needs FEM_F32 operators
+
+
+def test_pmg_zero_rhs_and_a_single_element():
+    # n = 1: the p = 1 level has no interior node (its coarse PCG sees an
+    # empty system), the p = 2 level one; b = 0 needs no iteration
+    meshes, gms, ops, pm, levels = _hierarchy(1, (4, 2, 1), coarse_its=5)
+    lmax = [opmg.power_lmax(L, 20) for L in levels[:-1]]
+    for l in range(2):
+        pm.set_lmax(l, lmax[l])
+    r = np.where(levels[0].inner, np.random.default_rng(9).uniform(-1, 1, levels[0].N), 0.0)
+    z = pm.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    ref = opmg.vcycle(levels, lmax + [0.0], r, degree=4, coarse_its=5)
+    assert rel(z, ref) <= 1e-10
+    b = torch.zeros(meshes[0]["N"], dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    st = pm.solve(b, x, rtol=1e-10)
+    assert st["status"] == "FEM_OK" and st["iterations"] == 0
+    assert torch.count_nonzero(x).item() == 0
