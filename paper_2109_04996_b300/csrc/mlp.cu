@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "mlp_gemm.cuh"
+#include "mlp_tc.cuh"
 
 using fem_mlp_k::GemmArgs;
 
@@ -38,6 +39,7 @@ struct fem_mlp {
   int64_t perm_cap = 0;
   float *y = nullptr;
   double *loss = nullptr;
+  int *tc_error = nullptr;        // set by a tensor-core GEMM whose wait ran out
   cudaStream_t stream = nullptr;
 };
 
@@ -123,6 +125,25 @@ int gemm(const fem_mlp *n, const GemmArgs &a, bool AT, bool BT) {
     fem_set_error("mlp gemm: K=%d (split %d) / leading dimensions not multiples of 32 / 8", a.K, a.ksplit);
     return FEM_EINVAL;
   }
+  if (n->mode == 0 && !AT && !BT && a.ksplit == 1 && !a.accumulate && !a.mask) {
+    // both operands K-major (the forward products): tcgen05 tensor cores
+    fem_mlp_tc::TcArgs t;
+    t.A = (const __nv_bfloat16 *)a.A; t.B = (const __nv_bfloat16 *)a.B;
+    t.lda = a.lda; t.ldb = a.ldb; t.M = a.M; t.N = a.N; t.K = a.K;
+    t.C = a.C; t.ldc = a.ldc; t.out_bf16 = a.out_bf16; t.bias = a.bias; t.relu = a.relu;
+    t.error = n->tc_error;
+    static bool attr = false;
+    if (!attr) {
+      FEM_CUDA_TRY(cudaFuncSetAttribute(fem_mlp_tc::gemm_tc_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, fem_mlp_tc::kSmemBytes));
+      attr = true;
+    }
+    dim3 grid((unsigned)((a.M + fem_mlp_tc::TM - 1) / fem_mlp_tc::TM),
+              (unsigned)((a.N + fem_mlp_tc::TN - 1) / fem_mlp_tc::TN));
+    fem_mlp_tc::gemm_tc_kernel<<<grid, fem_mlp_tc::NT, fem_mlp_tc::kSmemBytes, s>>>(t);
+    FEM_CHECK_LAUNCH();
+    return FEM_OK;
+  }
   if (n->mode == 0) {
     dim3 grid((unsigned)((a.M + 127) / 128), (unsigned)((a.N + 127) / 128), (unsigned)a.ksplit);
     if (!AT && !BT) fem_mlp_k::gemm_bf16_kernel<false, false><<<grid, 256, 0, s>>>(a);
@@ -170,6 +191,19 @@ int ensure_cap(fem_mlp *n, int64_t rows) {
 
 }  // namespace
 
+// Reads (and clears) the tensor-core GEMMs' timeout flag; synchronizes.
+int fem_mlp_check_tc(fem_mlp *n) {
+  int h = 0;
+  FEM_CUDA_TRY(cudaMemcpyAsync(&h, n->tc_error, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(n->stream));
+  if (h) {
+    FEM_CUDA_TRY(cudaMemsetAsync(n->tc_error, 0, sizeof(int), n->stream));
+    fem_set_error("mlp: a tensor-core GEMM's wait for its MMAs ran out");
+    return FEM_ETIMEOUT;
+  }
+  return FEM_OK;
+}
+
 // ---- internal entry points used by the preconditioner (fcg.cu)
 int fem_mlp_forward_rows(fem_mlp *n, const void *X, int64_t rows, float *Y) {
   const int b16 = n->mode == 0;
@@ -210,7 +244,8 @@ extern "C" fem_status fem_mlp_create(int n_in, int n_h, int n_out, int mode,
   if (cudaMalloc(&n->p, pb) != cudaSuccess || cudaMalloc(&n->g, pb) != cudaSuccess ||
       cudaMalloc(&n->m, pb) != cudaSuccess || cudaMalloc(&n->v, pb) != cudaSuccess ||
       cudaMalloc(&n->wq, esz(n) * n->np) != cudaSuccess ||
-      cudaMalloc(&n->loss, sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&n->loss, sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&n->tc_error, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     fem_mlp_destroy(n);
     fem_set_error("fem_mlp_create: allocation failed");
@@ -220,6 +255,7 @@ extern "C" fem_status fem_mlp_create(int n_in, int n_h, int n_out, int mode,
   cudaError_t e = cudaMemcpyAsync(n->p, params_host, pb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, pb, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, pb, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->tc_error, 0, sizeof(int), s);
   if (e != cudaSuccess) { fem_mlp_destroy(n); fem_set_error("fem_mlp_create: upload failed"); return FEM_ECUDA; }
   cast_weights_kernel<<<296, 256, 0, s>>>(n->p, off_b1(n), off_W2(n), off_b2(n), off_W3(n),
                                           off_b3(n), n->wq, mode == 0);
@@ -236,7 +272,7 @@ extern "C" fem_status fem_mlp_destroy(fem_mlp *n) {
   if (!n) return FEM_OK;
   cudaFree(n->p); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v); cudaFree(n->wq);
   cudaFree(n->h1); cudaFree(n->h2); cudaFree(n->dy); cudaFree(n->dh); cudaFree(n->y);
-  cudaFree(n->loss); cudaFree(n->xb); cudaFree(n->tb); cudaFree(n->perm);
+  cudaFree(n->loss); cudaFree(n->xb); cudaFree(n->tb); cudaFree(n->perm); cudaFree(n->tc_error);
   delete n;
   return FEM_OK;
 }
@@ -254,7 +290,9 @@ extern "C" fem_status fem_mlp_params(fem_mlp *n, float *params_host, int64_t *np
 extern "C" fem_status fem_mlp_forward(fem_mlp *n, const void *X, int64_t rows, float *Y) {
   if (!n || !X || !Y || rows < 0) { fem_set_error("fem_mlp_forward: invalid arguments"); return FEM_EINVAL; }
   if (rows == 0) return FEM_OK;
-  return fem_mlp_forward_rows(n, X, rows, Y);
+  int rc = fem_mlp_forward_rows(n, X, rows, Y);
+  if (rc) return rc;
+  return fem_mlp_check_tc(n);
 }
 
 // One training step on S rows: forward, loss, backward, Adam.  X [S][n_in]
@@ -406,5 +444,5 @@ extern "C" fem_status fem_mlp_train(fem_mlp *n, const void *X, const float *T, i
     }
     if (loss_host) loss_host[ep] = acc / steps;
   }
-  return FEM_OK;
+  return fem_mlp_check_tc(n);
 }

@@ -46,6 +46,19 @@ def test_forward_matches_oracle(mode, tol):
     assert rel(y, yr) <= tol
 
 
+@pytest.mark.parametrize("dims,S", [((160, 256, 128), 1000), ((256, 256, 256), 389), ((32, 128, 32), 129)])
+def test_tensor_core_forward_matches_oracle(dims, S):
+    # mode 0: the forward products run on tcgen05 (bf16 in, FP32 in tensor
+    # memory); the hidden activations are stored in bf16 between layers
+    p = fem_inputs.mlp_init(*dims, seed=4, out_scale=1.0)
+    net = fem.Mlp(*dims, p, mode=0)
+    x = np.random.default_rng(5).normal(0, 1, (S, dims[0]))
+    X = torch.from_numpy(x).to(net.input_dtype).cuda()
+    y = net.forward(X).double().cpu().numpy()
+    yr, _, _ = oracle.mlp_forward(dims, p.astype(np.float64), X.double().cpu().numpy())
+    assert rel(y, yr) <= 2e-2
+
+
 @pytest.mark.parametrize("mode,tol", [(1, 1e-5), (0, 5e-2)])
 def test_gradient_matches_oracle(mode, tol):
     p = fem_inputs.mlp_init(*DIMS, seed=2, out_scale=1.0)
