@@ -557,6 +557,26 @@ def run_profile(args):
     from paper_2109_04996_b300 import build as fembuild
     fembuild.build()
     import paper_2109_04996_b300 as fem
+    if args.profile.startswith("MLP:"):
+        # forward of the per-element network on `rows` element rows (the
+        # learned preconditioner's inference): MLP:n_in:n_h:n_out:rows
+        n_in, n_h, n_out, rows = (int(v) for v in args.profile.split(":")[1:])
+        net = fem.Mlp(n_in, n_h, n_out, fem_inputs.mlp_init(n_in, n_h, n_out, seed=1), mode=0)
+        X = torch.from_numpy(np.random.default_rng(0).normal(0, 1, (rows, n_in))).to(
+            net.input_dtype).cuda()
+        for _ in range(args.warmup):
+            net.forward(X)
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(args.steps):
+            net.forward(X)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        flops = 2.0 * rows * (n_in * n_h + n_h * n_h + n_h * n_out)
+        print(json.dumps({"profile": args.profile, "ms_per_forward": ms,
+                          "tflops": flops / ms / 1e9}))
+        return
     name, p, prec = args.profile.split(":")
     p = int(p)
     n = fem_inputs.bp3_mesh_n(args.dofs, p)
