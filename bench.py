@@ -743,7 +743,7 @@ def main():
                 "traffic_note": "DRAM bytes of one sweep (one FP64 apply per order), ncu counters"
                                 " of a 4e6-DOF capture per order scaled by algorithmic bytes",
                 "algorithmic_bytes": tot_bytes,
-                "kernel": "FP64 fused apply (slab body p<=5, line body p>=6), all orders",
+                "kernel": "FP64 fused apply (slab body p<=2, line body p>=3), all orders",
                 "hbm_achieved_gbs": tot_bytes / tot_time / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": tot_bytes / tot_time / 1e9 / hbm_peak,
                 "peak_source": "FP64 peak = 148 SMs x 2 FMA/clk x 2 flop x median SM clock;"

@@ -212,12 +212,14 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   const int P = op->P, Q = op->Q;
   const int64_t Q3 = (int64_t)Q * Q * Q;
   const int nd = kind == FEM_DIFFUSION ? 6 : 1;
-  // default launch shapes (measured): FP32 diffusion uses the line-based
-  // even-odd body; FP64 uses it from q = 8 on (Gauss), the slab body below
-  // and for the collocated operators, where its FP64 pipe use is lower
+  // default launch shapes (measured on B300, BP3 at 8e6 DOFs): FP32
+  // diffusion uses the line-based even-odd body; FP64 uses it from q = 5 on
+  // (Gauss; 1-6 % faster at p = 3..5), the slab body below (p = 1, 2: the
+  // even-odd saving is small and the slab's lower overhead wins, 8-11 %) and
+  // for the collocated operators
   if (kind == FEM_DIFFUSION) {
     op->tune_epb[FEM_F32] = 0;
-    op->tune_epb[FEM_F64] = (!op->colloc && Q >= 8) ? 0 : 3;
+    op->tune_epb[FEM_F64] = (!op->colloc && Q >= 5) ? 0 : 3;
   }
   int rc;
   double *tab = nullptr;

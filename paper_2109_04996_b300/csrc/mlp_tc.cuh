@@ -3,16 +3,19 @@
 //   FP32 accumulation in tensor memory, epilogue + bias[col], ReLU, store
 //   bf16 or fp32 to C [M][ldc].
 //
-// One CTA of 4 warps per 128 x 128 output tile.  K is staged 64 at a time:
-// every thread copies 16-byte row segments of A and B (cp.async, zero-filled
-// beyond M / N) into shared memory in the canonical no-swizzle K-major
-// layout -- 8-row x 16-byte core matrices, consecutive along K (leading
-// byte offset 128) and then along the rows (stride byte offset 1024) -- then
-// one thread issues four tcgen05.mma (kind::f16, M=128, N=128, K=16 each)
-// and a tcgen05.commit that arrives on an mbarrier.  The 128 x 128 FP32
-// accumulator lives in 128 TMEM columns (allocated per CTA); the epilogue
-// reads it with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows).
-// Every mbarrier wait is bounded: on expiry the CTA records an error, waits
+// One CTA of 4 warps per 128 x 128 output tile.  K is cut into 32-wide
+// stages held in a ring of NS shared-memory buffers: every thread copies
+// 16-byte row segments of A and B (cp.async, zero-filled beyond M, N or K)
+// into the canonical no-swizzle K-major layout -- 8-row x 16-byte core
+// matrices, consecutive along K (leading byte offset 128) and then along the
+// rows (stride byte offset 512) -- and the copies of the next NS-1 stages
+// stay in flight while one thread issues the current stage's two
+// tcgen05.mma (kind::f16, M=128, N=128, K=16 each) and a tcgen05.commit
+// that arrives on the stage buffer's mbarrier; a buffer is refilled once
+// that mbarrier shows its MMAs done.  The 128 x 128 FP32 accumulator lives
+// in 128 TMEM columns (allocated per CTA); the epilogue reads it with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows).  Every
+// mbarrier wait is bounded: on expiry the CTA records an error, waits
 // (bounded) for its own MMAs, frees its TMEM and returns.
 #pragma once
 #include <cuda_bf16.h>
@@ -20,9 +23,10 @@
 
 namespace fem_mlp_tc {
 
-constexpr int TM = 128, TN = 128, TK = 64, NT = 128;
-constexpr int kTileBytes = TM * TK * 2;           // 16 KB per operand stage
-constexpr int kSmemBytes = 56 * 1024;             // caps residency at 4 CTAs / SM (TMEM: 4 x 128 columns)
+constexpr int TM = 128, TN = 128, TK = 32, NT = 128, NS = 4;
+constexpr int kTileBytes = TM * TK * 2;           // 8 KB per operand and stage
+constexpr int kStageBytes = 2 * kTileBytes;       // A and B
+constexpr int kSmemBytes = NS * kStageBytes + 1024;   // 65 KB: 3 CTAs / SM (TMEM: 3 x 128 columns)
 constexpr unsigned long long kWaitLimit = 1ull << 22;   // try_wait polls before giving up
 
 struct TcArgs {
@@ -73,19 +77,48 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// cp.async.wait_group with a run-time count of groups allowed to stay pending
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  if (n <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  else if (n == 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+  else asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+}
+
+// Copies of K stage `st` (columns [st*TK, st*TK + TK)) into stage buffer b.
+__device__ __forceinline__ void load_stage(const TcArgs &g, unsigned char *buf, int st, int64_t row0,
+                                           int col0) {
+  unsigned char *sA = buf, *sB = buf + kTileBytes;
+  const int kbase = st * TK;
+#pragma unroll
+  for (int c = 0; c < (TM * TK / 8) / NT; c++) {
+    const int chunk = threadIdx.x + c * NT;          // 0 .. 511
+    const int r = chunk / (TK / 8), k8 = chunk % (TK / 8);   // row, 8-element segment
+    const uint32_t off = (uint32_t)(((r >> 3) * (TK / 8) + k8) * 128 + (r & 7) * 16);
+    const int kc = kbase + k8 * 8;
+    const bool vk = kc < g.K;
+    const int64_t ra = row0 + r;
+    const bool va = vk && ra < g.M;
+    cp_async16(smem_u32(sA + off), g.A + (va ? ra * g.lda + kc : 0), va);
+    const int rb = col0 + r;
+    const bool vb = vk && rb < g.N;
+    cp_async16(smem_u32(sB + off), g.B + (vb ? (int64_t)rb * g.ldb + kc : 0), vb);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[NS];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
-  unsigned char *sA = smem, *sB = smem + kTileBytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row0 = (int64_t)blockIdx.x * TM;
   const int col0 = blockIdx.y * TN;
-  const uint32_t bar = smem_u32(&mbar);
   if (threadIdx.x == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    for (int b = 0; b < NS; b++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[b])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -97,37 +130,26 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const int nstages = (g.K + TK - 1) / TK;   // K segments past K are zero-filled
-  uint32_t phase = 0;
-  for (int st = 0; st < nstages; st++) {
-    // ---- stage K columns [st*TK, st*TK + TK) of A and B into shared memory
-    const int kbase = st * TK;
-#pragma unroll
-    for (int c = 0; c < (TM * TK / 8) / NT; c++) {
-      const int chunk = threadIdx.x + c * NT;          // 0 .. 1023
-      const int r = chunk >> 3, k8 = chunk & 7;          // row, 8-element segment
-      const uint32_t off = (uint32_t)(((r >> 3) * (TK / 8) + k8) * 128 + (r & 7) * 16);
-      const int kc = kbase + k8 * 8;
-      const bool vk = kc < g.K;
-      const int64_t ra = row0 + r;
-      const bool va = vk && ra < g.M;
-      cp_async16(smem_u32(sA + off), g.A + (va ? ra * g.lda + kc : 0), va);
-      const int rb = col0 + r;
-      const bool vb = vk && rb < g.N;
-      cp_async16(smem_u32(sB + off), g.B + (vb ? (int64_t)rb * g.ldb + kc : 0), vb);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  const int nst = (g.K + TK - 1) / TK;   // K segments past K are zero-filled
+  // prologue: the first NS stages in flight
+  int issued = 0;
+  int committed = -1;   // the stage whose MMAs were committed last
+  for (; issued < NS && issued < nst; issued++) load_stage(g, smem + issued * kStageBytes, issued, row0, col0);
+  for (int st = 0; st < nst; st++) {
+    const int b = st % NS;
+    // stage st's copies done (later groups may stay pending)
+    cp_async_wait_pending(issued - st - 1);
     // generic-proxy writes of shared memory -> visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t base = smem_u32(smem + b * kStageBytes);
 #pragma unroll
       for (int kk = 0; kk < TK / 16; kk++) {
         // K = 16 per instruction: two core matrices along K (256 bytes)
-        const uint64_t ad = smem_desc(smem_u32(sA) + kk * 256, 128, (TK / 8) * 128);
-        const uint64_t bd = smem_desc(smem_u32(sB) + kk * 256, 128, (TK / 8) * 128);
+        const uint64_t ad = smem_desc(base + kk * 256, 128, (TK / 8) * 128);
+        const uint64_t bd = smem_desc(base + kTileBytes + kk * 256, 128, (TK / 8) * 128);
         const uint32_t acc = (st > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -135,24 +157,48 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
             "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
             : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&mbar[b]))
                    : "memory");
     }
-    // the stage buffers are reused: wait for these MMAs to finish; if the
-    // wait runs out, record it and give the MMAs in flight a second bounded
-    // wait before the TMEM they write is freed
-    if (!mbar_wait(bar, phase)) {
-      if (threadIdx.x == 0) { s_fail = 1; atomicExch(g.error, 1); }
-      mbar_wait(bar, phase);
+    committed = st;
+    // refill the buffer of stage st - 1 (its MMAs were issued one step ago)
+    // with stage st - 1 + NS, once those MMAs are done
+    const int sp = st - 1;
+    if (sp >= 0 && sp + NS < nst) {
+      const int bp = sp % NS;
+      if (!mbar_wait(smem_u32(&mbar[bp]), (uint32_t)((sp / NS) & 1))) {
+        if (threadIdx.x == 0) { s_fail = 1; atomicExch(g.error, 1); }
+      }
+      __syncthreads();
+      if (s_fail) break;
+      load_stage(g, smem + bp * kStageBytes, sp + NS, row0, col0);
+      issued++;
     }
-    phase ^= 1;
-    __syncthreads();
-    if (s_fail) break;
   }
+  // the last commit covers every MMA issued before it; after a failed wait
+  // it is the MMAs' second (bounded) wait before their TMEM is freed
+  if (committed >= 0) {
+    const uint32_t bl = smem_u32(&mbar[committed % NS]), par = (uint32_t)((committed / NS) & 1);
+    if (!mbar_wait(bl, par)) {
+      if (threadIdx.x == 0) { s_fail = 1; atomicExch(g.error, 1); }
+      mbar_wait(bl, par);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (!s_fail) {
-    // ---- epilogue: warp w reads tile rows 32w + lane, 32 columns at a time
-    const int64_t row = row0 + warp * 32 + lane;
+    // ---- epilogue.  The stage buffers are free now: the bias of the tile's
+    // columns and one 32-column chunk of the accumulator at a time are
+    // staged there, so that each warp can store its 32 rows with the lanes
+    // along the columns (coalesced) instead of one row per lane.
+    float *stile = reinterpret_cast<float *>(smem);        // [128][33]
+    float *sbias = stile + TM * 33;                          // [TN]
+    for (int i = threadIdx.x; i < TN; i += NT)
+      sbias[i] = (g.bias && col0 + i < g.N) ? g.bias[col0 + i] : 0.0f;
+    __syncthreads();
+    const int rloc = warp * 32 + lane;                      // this thread's TMEM lane = tile row
 #pragma unroll 1
     for (int cb = 0; cb < TN; cb += 32) {
       uint32_t v[32];
@@ -167,21 +213,24 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
             "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (row < g.M) {
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
-          const int col = col0 + cb + j;
-          if (col < g.N) {
-            float x = __uint_as_float(v[j]);
-            if (g.bias) x += g.bias[col];
-            if (g.relu) x = x > 0.0f ? x : 0.0f;
-            if (g.out_bf16)
-              reinterpret_cast<__nv_bfloat16 *>(g.C)[row * g.ldc + col] = __float2bfloat16(x);
-            else
-              reinterpret_cast<float *>(g.C)[row * g.ldc + col] = x;
-          }
+      for (int j = 0; j < 32; j++) stile[rloc * 33 + j] = __uint_as_float(v[j]);
+      __syncwarp();
+      const int col = col0 + cb + lane;
+      const float bcol = sbias[cb + lane];
+#pragma unroll 4
+      for (int rr = 0; rr < 32; rr++) {
+        const int64_t row = row0 + warp * 32 + rr;
+        if (row < g.M && col < g.N) {
+          float x = stile[(warp * 32 + rr) * 33 + lane] + bcol;
+          if (g.relu) x = x > 0.0f ? x : 0.0f;
+          if (g.out_bf16)
+            reinterpret_cast<__nv_bfloat16 *>(g.C)[row * g.ldc + col] = __float2bfloat16(x);
+          else
+            reinterpret_cast<float *>(g.C)[row * g.ldc + col] = x;
         }
       }
+      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
