@@ -151,14 +151,14 @@ FP64_FMA_PER_SM_CLK = 2.0
 # bytes are qdata, indices and the two vectors, all proportional to the mesh),
 # so the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 5374304000, 68418816),
-    2: (493039, 4019679, 1661111040, 46400512),
-    3: (148877, 4096000, 1006866432, 36539136),
-    4: (59319, 3869893, 712461824, 31814656),
-    5: (32768, 4173281, 634934272, 30916352),
-    6: (17576, 3869893, 524028416, 30568960),
-    7: (12167, 4251528, 523802624, 31756288),
-    8: (8000, 4173281, 476999936, 30838272),
+    1: (3944312, 4019679, 5374437376, 68375040),
+    2: (493039, 4019679, 1661260800, 46460416),
+    3: (148877, 4096000, 1019672832, 43075840),
+    4: (59319, 3869893, 713128704, 31546112),
+    5: (32768, 4173281, 638709248, 32124160),
+    6: (17576, 3869893, 522269184, 30345728),
+    7: (12167, 4251528, 524337408, 31831296),
+    8: (8000, 4173281, 476937216, 30977024),
 }
 
 
