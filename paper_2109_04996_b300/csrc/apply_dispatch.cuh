@@ -45,11 +45,11 @@ int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
 }
 
 // Diffusion: the line-based, even-odd element body (apply_lines.cuh).
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE>
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND>
 int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
-  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE>;
+  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND>;
   static int max_bps = -1;
   if (max_bps < 0) {
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -68,7 +68,7 @@ int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   return FEM_OK;
 }
 
-template <typename T, int P, int Q, bool COLLOC, int EPB>
+template <typename T, int P, int Q, bool COLLOC, int EPB, int KIND>
 int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
@@ -89,21 +89,22 @@ int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
     make_symtab<T, Q, Q>(Dt, lp.t.Dt);
     if constexpr (sizeof(T) == 4) {
       if (prm.ncomp == 1 && !prm.list)
-        return launch_lines_kernel<T, P, Q, COLLOC, EPB, true>(op, lp, bps);
+        return launch_lines_kernel<T, P, Q, COLLOC, EPB, true, KIND>(op, lp, bps);
     }
-    return launch_lines_kernel<T, P, Q, COLLOC, EPB, false>(op, lp, bps);
+    return launch_lines_kernel<T, P, Q, COLLOC, EPB, false, KIND>(op, lp, bps);
   }
 }
 
 // Launch shape choice: 0..2 the line-based body with the three EPB
-// candidates, 3..5 the slab body (diffusion); mass has only the slab body.
+// candidates, 3..5 the slab body; the collocated mass operator (pointwise)
+// has only the slab body.
 template <typename T, int P, int Q, int KIND, bool COLLOC>
 int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
-  if constexpr (KIND == FEM_DIFFUSION) {
+  if constexpr (KIND == FEM_DIFFUSION || !COLLOC) {
     switch (choice) {
-      case 0: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 0>::value>(op, prm, bps);
-      case 1: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 1>::value>(op, prm, bps);
-      case 2: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);
+      case 0: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps);
+      case 1: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps);
+      case 2: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps);
       case 4: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 1>::value>(op, prm, bps);
       case 5: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);
       default: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 0>::value>(op, prm, bps);
@@ -116,7 +117,8 @@ int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
   }
 }
 
-// Diffusion shapes are tunable; mass and the q = p+1 Gauss variant use the default.
+// Launch shapes are tunable (epb_choices) except for the collocated mass
+// operator, which is pointwise.
 template <typename T, int P>
 int dispatch_q(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
   constexpr int QG = (P + 1 <= FEM_MAX_Q) ? P + 1 : P;
@@ -126,11 +128,11 @@ int dispatch_q(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
       return diff ? launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps)
                   : launch_shape<T, P, P, FEM_MASS, true, EpbChoice<P, 0>::value>(op, prm, bps);
     return diff ? launch_epb<T, P, P, FEM_DIFFUSION, false>(op, prm, choice, bps)
-                : launch_shape<T, P, P, FEM_MASS, false, EpbChoice<P, 0>::value>(op, prm, bps);
+                : launch_epb<T, P, P, FEM_MASS, false>(op, prm, choice, bps);
   }
   if (op->Q == P + 1 && QG == P + 1)
     return diff ? launch_epb<T, P, QG, FEM_DIFFUSION, false>(op, prm, choice, bps)
-                : launch_shape<T, P, QG, FEM_MASS, false, EpbChoice<QG, 0>::value>(op, prm, bps);
+                : launch_epb<T, P, QG, FEM_MASS, false>(op, prm, choice, bps);
   fem_set_error("apply: unsupported (P, q) = (%d, %d)", P, op->Q);
   return FEM_EINVAL;
 }
@@ -153,7 +155,7 @@ int dispatch(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
 
 // Number of launch shape choices for this operator.
 inline int epb_choices(const fem_op *op) {
-  return op->kind == FEM_DIFFUSION ? 6 : (op->colloc ? 1 : 3);
+  return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
 }
 
 }  // namespace fem_apply

@@ -163,12 +163,17 @@ __device__ __forceinline__ void column_values(const ApplyParams<T> &prm, Column<
 // given in `cur` (ids and values loaded by the previous iteration) and the
 // next group's (g + gridDim.x) is loaded into `nxt`: its ids at the start,
 // its values after the gradient stage.
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE = false, bool PAD = true>
+// KIND: FEM_DIFFUSION (gradients, 6 qdata per point) or FEM_MASS (values,
+// 1 qdata per point: the interpolation stages only; not collocated).
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE = false, bool PAD = true,
+          int KIND = FEM_DIFFUSION>
 __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
                                                   const LineTables<T, P, Q> &tb, int64_t g,
                                                   T *cubes, double &dot,
                                                   const Column<T, P> *cur = nullptr,
                                                   Column<T, P> *nxt = nullptr) {
+  constexpr bool DIFF = KIND == FEM_DIFFUSION;
+  static_assert(DIFF || !COLLOC, "the collocated mass operator is pointwise: slab body");
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P2 = P * P, P3 = P * P * P;
   constexpr int CS = LineCube<Q, PAD>::size, PITCH = LineCube<Q, PAD>::pitch;
   const int slot_raw = threadIdx.x / Q2;
@@ -182,7 +187,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   int64_t e = 0;
   if (valid) e = prm.list ? (int64_t)prm.list[k_el] : k_el;
   const int32_t *en = prm.elem_nodes + e * P3;
-  const T *qd = prm.qdata + e * (int64_t)(6 * Q3);
+  const T *qd = prm.qdata + e * (int64_t)((DIFF ? 6 : 1) * Q3);
   // line coordinates of this thread: (t % Q, t / Q) for q-by-q line sets,
   // (t % P, t / P) for P-by-q, (t % P, t / P) for P-by-P
   const int lq0 = t % Q, lq1 = t / Q;
@@ -243,6 +248,19 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       }
     }
     __syncthreads();
+    if constexpr (!DIFF) {
+      if constexpr (PIPE) column_values<T, P>(prm, *nxt);
+      // ---- mass: values at the quadrature points times w detJ, in place
+      if (on_qq) {
+#pragma unroll
+        for (int kq = 0; kq < Q; kq++) {
+          const int pt = cube_ix<Q, PITCH>(kq, lq1, lq0);
+          const T w = valid ? qd[(kq * Q + lq1) * Q + lq0] : T(0);
+          c3[pt] *= w;
+        }
+      }
+      __syncthreads();
+    } else {
     // ---- reference gradients: x into c1, y into c2, z into c4
     if (on_qq) {
       T in[Q], out[Q];
@@ -306,6 +324,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       for (int m = 0; m < Q; m++) c4[cube_ix<Q, PITCH>(m, lq1, lq0)] = out[m];
     }
     __syncthreads();
+    }  // DIFF
     if constexpr (COLLOC) {
       // sum of the three contributions at the node column (a, b), scatter
       if (on_pp) {
@@ -330,7 +349,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
 #pragma unroll
         for (int m = 0; m < Q; m++) {
           const int pt = cube_ix<Q, PITCH>(lq1, lq0, m);
-          in[m] = c1[pt] + c2[pt] + c4[pt];
+          in[m] = DIFF ? c1[pt] + c2[pt] + c4[pt] : c3[pt];
         }
         sym_apply<+1>(tb.Bt, in, out);
 #pragma unroll
@@ -373,7 +392,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
 // (scalar operators over contiguous elements; the launcher picks it for FP32,
 // whose time is load latency); a separate instantiation, so that the others
 // keep their lower register count.
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE>
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND>
 __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     fem_apply_lines_kernel(const LineParams<T, P, Q> lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -386,12 +405,12 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     column_indices<T, P, Q, EPB>(prm, blockIdx.x, cur);
     column_values<T, P>(prm, cur);
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-      apply_group_lines<T, P, Q, COLLOC, EPB, true>(prm, lp.t, g, cubes, dot, &cur, &nxt);
+      apply_group_lines<T, P, Q, COLLOC, EPB, true, true, KIND>(prm, lp.t, g, cubes, dot, &cur, &nxt);
       cur = nxt;
     }
   } else {
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
-      apply_group_lines<T, P, Q, COLLOC, EPB>(prm, lp.t, g, cubes, dot);
+      apply_group_lines<T, P, Q, COLLOC, EPB, false, true, KIND>(prm, lp.t, g, cubes, dot);
   }
   if (prm.dot_out) {
     double v[1] = {dot};

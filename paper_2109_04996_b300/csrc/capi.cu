@@ -220,6 +220,12 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   if (kind == FEM_DIFFUSION) {
     op->tune_epb[FEM_F32] = 0;
     op->tune_epb[FEM_F64] = (!op->colloc && Q >= 5) ? 0 : 3;
+  } else if (!op->colloc) {
+    // mass (BP1 at 8e6 DOFs): FP32 line body with half the default elements
+    // per block (2.4-3.2x the slab body for p >= 4); FP64 line body from
+    // q = 5 (half the elements per block from q = 9), slab body below
+    op->tune_epb[FEM_F32] = 1;
+    op->tune_epb[FEM_F64] = Q >= 9 ? 1 : (Q >= 5 ? 0 : 3);
   }
   int rc;
   double *tab = nullptr;

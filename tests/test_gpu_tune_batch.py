@@ -30,7 +30,8 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("name,p,n", [("BP3", 3, 3), ("BP5", 7, 2), ("BP3", 8, 2)])
+@pytest.mark.parametrize("name,p,n", [("BP3", 3, 3), ("BP5", 7, 2), ("BP3", 8, 2), ("BP1", 3, 3),
+                                      ("BP1", 8, 2), ("BP1", 1, 5)])
 @pytest.mark.parametrize("prec", [fem.F64, fem.F32])
 def test_every_launch_shape_matches_oracle(name, p, n, prec):
     kind, ncomp, quad, dq = fem.BAKE_OFF[name]
