@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--tts-dofs", type=float, default=1e7,
                     help="size of the time-to-1e-10 comparison (0 = skip)")
     ap.add_argument("--tts-order", type=int, default=4)
-    ap.add_argument("--sections", default="bp56,suite,batched,learned",
-                    help="extra measured configurations: bp56, suite, batched, learned (comma list)")
+    ap.add_argument("--sections", default="bp56,suite,nsweep,batched,learned",
+                    help="extra measured configurations: bp56, suite, nsweep, batched, learned"
+                         " (comma list)")
     ap.add_argument("--bp56-n", type=int, default=44, help="elements per direction, BP5/BP6 p=7")
     ap.add_argument("--suite-order", type=int, default=4, help="order of the BP1-BP6 suite section")
     ap.add_argument("--suite-dofs", type=float, default=8e6, help="nodes of the BP1-BP6 suite mesh")
@@ -192,9 +193,41 @@ def cpu_baseline(work, iters, seconds, seed=0):
         total_t += t_elem * E * iters
         total_dof_it += N * iters
         sample.append("p=%d: %d elements in %.1fs" % (p, ne, t))
+    # the same oracle with its element matrices computed once and kept
+    # (batched dense products): the rate where they fit in memory
+    cached_t, cached_dof_it = 0.0, 0.0
+    for p, n in work:
+        if p > 6:
+            continue
+        N, E, _, _ = algorithmic(p, n)
+        m = fem_inputs.box_mesh(3, p, perturb=0.1, seed=seed)
+        op = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, p + 2, nthreads=cores)
+        K = np.stack([op.element_matrix(e) for e in range(m["E"])])
+        en = m["elem_nodes"]
+        x = fem_inputs.rhs_uniform(m["N"], None, seed=seed)
+        reps, t = 0, 0.0
+        while t < min(1.0, per):
+            t0 = time.perf_counter()
+            y = np.zeros(m["N"])
+            np.add.at(y, en, np.matmul(K, x[en][..., None])[..., 0])
+            t += time.perf_counter() - t0
+            reps += 1
+        cached_t += t / (reps * m["E"]) * E * iters
+        cached_dof_it += N * iters
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
     return {"value": total_dof_it / total_t / 1e9, "unit": "GDOF/s", "cores": cores,
-            "kind": "oracle", "sample": "; ".join(sample) +
-            " (brute-force element apply, extrapolated to every element x iterations)"}
+            "kind": "oracle", "cpu_model": model,
+            "cached_element_matrices_gdofs": (cached_dof_it / cached_t / 1e9) if cached_t else None,
+            "sample": "; ".join(sample) +
+            " (brute-force element apply, extrapolated to every element x iterations;"
+            " cached_element_matrices_gdofs: the same with stored K_e, p <= 6)"}
 
 
 def run_reference(args):
@@ -356,6 +389,42 @@ def section_bp56(fem, torch, args):
             "time_to_1e-10": tts,
             "speedup_refined_vs_fp64": tts["fp64_pcg"]["seconds"] / tts["fp32_refined"]["seconds"]}
         del op, x, y, x32, y32, b
+    return out
+
+
+def section_nsweep(fem, torch, args):
+    """Throughput against problem size (the paper's throughput-vs-time plots
+    of the BP3 runs): FP64 Jacobi-PCG iterations (graph-captured, 20 per
+    measurement) on BP3 meshes of 1e4 .. 3e7 DOFs at p = 2, 4, 8; per size
+    the time per iteration and DOFs x iterations / s, and per order n_0.8,
+    the smallest size reaching 80 % of that order's best rate."""
+    out = {}
+    targets = [1e4, 3e4, 1e5, 3e5, 1e6, 3e6, 1e7, 3e7]
+    iters = 20
+    for p in (2, 4, 8):
+        rows = []
+        for t in targets:
+            n = max(1, fem_inputs.bp3_mesh_n(t, p))
+            m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=710 + p)
+            op = fem.Operator.bake_off(fem.Mesh(m), "BP3")
+            b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=711)).cuda()
+            x = torch.zeros_like(b)
+            op.cg(b, x, precond=fem.PC_JACOBI, maxit=iters, rtol=0.0)   # builds the graph
+            best = None
+            for _ in range(3):
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = op.cg(b, x, precond=fem.PC_JACOBI, maxit=iters, rtol=0.0)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            rows.append({"dofs": m["N"], "seconds_per_iteration": best / st["iterations"],
+                         "gdofs": m["N"] * st["iterations"] / best / 1e9})
+            del op, m, b, x
+        peak = max(r["gdofs"] for r in rows)
+        n08 = min((r["dofs"] for r in rows if r["gdofs"] >= 0.8 * peak), default=None)
+        out["p%d" % p] = {"points": rows, "best_gdofs": peak, "n_0.8_dofs": n08}
     return out
 
 
@@ -764,6 +833,8 @@ def main():
         line["bp5_bp6"] = section_bp56(fem, torch, args)
     if "suite" in secs:
         line["bp_suite"] = section_suite(fem, torch, args)
+    if "nsweep" in secs:
+        line["size_sweep"] = section_nsweep(fem, torch, args)
     if "batched" in secs:
         line["batched"] = section_batched(fem, torch, args)
     if "learned" in secs:
