@@ -38,7 +38,7 @@ def make(name, n, p, seed=7, shuffle=None):
 
 
 CASES = ([("BP3", p) for p in range(1, 9)] + [("BP5", p) for p in (1, 3, 7, 8)] +
-         [("BP1", 2), ("BP1", 6), ("BP6", 7), ("BP2", 2)])
+         [("BP1", 2), ("BP1", 6), ("BP6", 7), ("BP2", 2), ("BP4", 1)])
 
 
 @pytest.mark.parametrize("name,p", CASES)

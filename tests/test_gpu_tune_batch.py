@@ -31,7 +31,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("name,p,n", [("BP3", 3, 3), ("BP5", 7, 2), ("BP3", 8, 2), ("BP1", 3, 3),
-                                      ("BP1", 8, 2), ("BP1", 1, 5)])
+                                      ("BP1", 8, 2), ("BP1", 1, 5), ("BP3", 1, 6)])
 @pytest.mark.parametrize("prec", [fem.F64, fem.F32])
 def test_every_launch_shape_matches_oracle(name, p, n, prec):
     kind, ncomp, quad, dq = fem.BAKE_OFF[name]
