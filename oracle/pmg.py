@@ -62,14 +62,15 @@ def interpolation_1d(pc, pf):
 
 
 class Level:
-    """One level: its mesh (fem_inputs.box_mesh dict) and operator."""
+    """One level: its mesh (fem_inputs.box_mesh dict) and operator (Gauss
+    rule of q points per direction, q = p + 2 unless given)."""
 
-    def __init__(self, mesh, kind=DIFFUSION, rff=None):
+    def __init__(self, mesh, kind=DIFFUSION, rff=None, q=None):
         p = mesh["p"]
         self.mesh = mesh
         self.p = p
         self.N = mesh["N"]
-        self.op = Operator(mesh, kind, GAUSS, p + 2, rff=rff)
+        self.op = Operator(mesh, kind, GAUSS, p + 2 if q is None else q, rff=rff)
         self.inner = mesh["dirichlet"] == 0
         d = self.op.diagonal()
         self.diag = np.where(self.inner, d, 0.0)

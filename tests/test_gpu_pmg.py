@@ -31,12 +31,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def _hierarchy(n, orders, prec=fem.F64, seed=3, **kw):
+def _hierarchy(n, orders, prec=fem.F64, seed=3, coarse_dq=2, **kw):
+    # the finest level is BP3 (q = p + 2); coarse levels use q = p + coarse_dq
     meshes = [fem_inputs.box_mesh(n, p, perturb=0.1, seed=seed) for p in orders]
     gms = [fem.Mesh(m) for m in meshes]
-    ops = [fem.Operator.bake_off(g, "BP3", prec=prec) for g in gms]
+    ops = [fem.Operator(g, fem.DIFFUSION, fem.GAUSS, g.p + (2 if l == 0 else coarse_dq), prec=prec)
+           for l, g in enumerate(gms)]
     pm = fem.Pmg(ops, prec=prec, **kw)
-    levels = [opmg.Level(m) for m in meshes]
+    levels = [opmg.Level(m, q=m["p"] + (2 if l == 0 else coarse_dq)) for l, m in enumerate(meshes)]
     return meshes, gms, ops, pm, levels
 
 
@@ -74,6 +76,19 @@ def test_vcycle_fp64_matches_oracle(orders, degree, coarse_its):
     ref = opmg.vcycle(levels, lmax, r, degree=degree, coarse_its=coarse_its)
     assert rel(z, ref) <= 1e-10
     assert np.all(z[~levels[0].inner] == 0.0)
+
+
+@pytest.mark.parametrize("orders", [(4, 2, 1), (8, 4, 2, 1)])
+def test_vcycle_with_coarse_levels_on_p_plus_1_points_matches_oracle(orders):
+    # coarse levels rediscretized with Gauss q = p + 1 (exact for affine bricks)
+    meshes, gms, ops, pm, levels = _hierarchy(4, orders, coarse_dq=1, coarse_its=10)
+    lmax = [opmg.power_lmax(L, 20) for L in levels[:-1]]
+    for l in range(len(orders) - 1):
+        pm.set_lmax(l, lmax[l])
+    r = np.where(levels[0].inner, np.random.default_rng(11).uniform(-1, 1, levels[0].N), 0.0)
+    z = pm.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    ref = opmg.vcycle(levels, lmax + [0.0], r, degree=4, coarse_its=10)
+    assert rel(z, ref) <= 1e-10
 
 
 def test_vcycle_fp32_matches_oracle():
