@@ -40,6 +40,8 @@ struct fem_mlp {
   float *y = nullptr;
   double *loss = nullptr;
   int *tc_error = nullptr;        // set by a tensor-core GEMM whose wait ran out
+  void *tA = nullptr, *tB = nullptr;   // K-major copies of transposed GEMM operands
+  int64_t tcapA = 0, tcapB = 0;
   cudaStream_t stream = nullptr;
 };
 
@@ -125,13 +127,53 @@ int gemm(const fem_mlp *n, const GemmArgs &a, bool AT, bool BT) {
     fem_set_error("mlp gemm: K=%d (split %d) / leading dimensions not multiples of 32 / 8", a.K, a.ksplit);
     return FEM_EINVAL;
   }
-  if (n->mode == 0 && !AT && !BT && a.ksplit == 1 && !a.accumulate && !a.mask) {
-    // both operands K-major (the forward products): tcgen05 tensor cores
+  if (n->mode == 0 && !(AT && !BT)) {
+    // tcgen05 tensor cores.  The kernel takes both operands K-major; an
+    // operand stored the other way ([K][M] or [K][N]: the backward products)
+    // is first transposed into a scratch copy.
     fem_mlp_tc::TcArgs t;
-    t.A = (const __nv_bfloat16 *)a.A; t.B = (const __nv_bfloat16 *)a.B;
-    t.lda = a.lda; t.ldb = a.ldb; t.M = a.M; t.N = a.N; t.K = a.K;
-    t.C = a.C; t.ldc = a.ldc; t.out_bf16 = a.out_bf16; t.bias = a.bias; t.relu = a.relu;
+    const __nv_bfloat16 *A = (const __nv_bfloat16 *)a.A, *B = (const __nv_bfloat16 *)a.B;
+    int64_t lda = a.lda, ldb = a.ldb;
+    auto scratch = [&](void **buf, int64_t *cap, int64_t elems) -> bool {
+      if (*cap >= elems) return true;
+      cudaFree(*buf);
+      *buf = nullptr; *cap = 0;
+      if (cudaMalloc(buf, sizeof(__nv_bfloat16) * (size_t)elems) != cudaSuccess) { cudaGetLastError(); return false; }
+      *cap = elems;
+      return true;
+    };
+    fem_mlp *nm = const_cast<fem_mlp *>(n);
+    const dim3 tb(32, 8);
+    if (AT) {   // A stored [K][M]
+      if (!scratch(&nm->tA, &nm->tcapA, a.M * (int64_t)a.K)) { fem_set_error("mlp gemm: scratch allocation failed"); return FEM_ENOMEM; }
+      fem_mlp_tc::transpose_bf16_kernel<<<dim3((unsigned)((a.K + 31) / 32), (unsigned)((a.M + 31) / 32)), tb, 0, s>>>(
+          A, a.K, (int)a.M, lda, (__nv_bfloat16 *)nm->tA, a.K);
+      A = (const __nv_bfloat16 *)nm->tA; lda = a.K;
+    }
+    if (BT) {   // B stored [K][N]
+      if (!scratch(&nm->tB, &nm->tcapB, (int64_t)a.N * a.K)) { fem_set_error("mlp gemm: scratch allocation failed"); return FEM_ENOMEM; }
+      fem_mlp_tc::transpose_bf16_kernel<<<dim3((unsigned)((a.K + 31) / 32), (unsigned)((a.N + 31) / 32)), tb, 0, s>>>(
+          B, a.K, a.N, ldb, (__nv_bfloat16 *)nm->tB, a.K);
+      B = (const __nv_bfloat16 *)nm->tB; ldb = a.K;
+    }
+    t.A = A; t.B = B; t.lda = lda; t.ldb = ldb; t.M = a.M; t.N = a.N; t.K = a.K;
+    t.C = a.C; t.ldc = a.ldc; t.out_bf16 = a.out_bf16; t.accumulate = a.accumulate;
+    t.bias = a.bias; t.relu = a.relu;
+    t.mask = (const __nv_bfloat16 *)a.mask; t.ldm = a.ldm;
     t.error = n->tc_error;
+    const int64_t tiles = ((a.M + fem_mlp_tc::TM - 1) / fem_mlp_tc::TM) * ((a.N + fem_mlp_tc::TN - 1) / fem_mlp_tc::TN);
+    int ks = 1;
+    if (a.accumulate) {
+      // few output tiles and a long K (the weight gradients): split K so that
+      // about three CTAs per SM run, each K chunk a multiple of the stage
+      const int64_t want = (int64_t)3 * 148 / (tiles > 0 ? tiles : 1);
+      const int64_t maxks = (a.K + fem_mlp_tc::TK - 1) / fem_mlp_tc::TK;
+      ks = (int)(want < 1 ? 1 : (want > maxks ? maxks : want));
+    }
+    int kchunk = (a.K + ks - 1) / ks;
+    kchunk = (kchunk + fem_mlp_tc::TK - 1) / fem_mlp_tc::TK * fem_mlp_tc::TK;
+    ks = (a.K + kchunk - 1) / kchunk;
+    t.kchunk = kchunk;
     static bool attr = false;
     if (!attr) {
       FEM_CUDA_TRY(cudaFuncSetAttribute(fem_mlp_tc::gemm_tc_kernel,
@@ -139,7 +181,7 @@ int gemm(const fem_mlp *n, const GemmArgs &a, bool AT, bool BT) {
       attr = true;
     }
     dim3 grid((unsigned)((a.M + fem_mlp_tc::TM - 1) / fem_mlp_tc::TM),
-              (unsigned)((a.N + fem_mlp_tc::TN - 1) / fem_mlp_tc::TN));
+              (unsigned)((a.N + fem_mlp_tc::TN - 1) / fem_mlp_tc::TN), (unsigned)ks);
     fem_mlp_tc::gemm_tc_kernel<<<grid, fem_mlp_tc::NT, fem_mlp_tc::kSmemBytes, s>>>(t);
     FEM_CHECK_LAUNCH();
     return FEM_OK;
@@ -273,6 +315,7 @@ extern "C" fem_status fem_mlp_destroy(fem_mlp *n) {
   cudaFree(n->p); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v); cudaFree(n->wq);
   cudaFree(n->h1); cudaFree(n->h2); cudaFree(n->dy); cudaFree(n->dh); cudaFree(n->y);
   cudaFree(n->loss); cudaFree(n->xb); cudaFree(n->tb); cudaFree(n->perm); cudaFree(n->tc_error);
+  cudaFree(n->tA); cudaFree(n->tB);
   delete n;
   return FEM_OK;
 }

@@ -33,11 +33,15 @@ struct TcArgs {
   const __nv_bfloat16 *A, *B;
   int64_t lda, ldb, M;
   int N, K;
+  int kchunk;           // K columns per blockIdx.z (split-K; multiple of TK)
   void *C;
   int64_t ldc;
   int out_bf16;
+  int accumulate;       // 1: atomic-add into fp32 C (split-K), no bias / ReLU
   const float *bias;
   int relu;
+  const __nv_bfloat16 *mask;   // times (mask[row][col] > 0), or null
+  int64_t ldm;
   int *error;           // set to 1 if a wait ran out
 };
 
@@ -85,18 +89,19 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
   else asm volatile("cp.async.wait_group 3;\n" ::: "memory");
 }
 
-// Copies of K stage `st` (columns [st*TK, st*TK + TK)) into stage buffer b.
+// Copies of K stage `st` (columns [k0 + st*TK, k0 + st*TK + TK), below
+// kend) into stage buffer b.
 __device__ __forceinline__ void load_stage(const TcArgs &g, unsigned char *buf, int st, int64_t row0,
-                                           int col0) {
+                                           int col0, int k0, int kend) {
   unsigned char *sA = buf, *sB = buf + kTileBytes;
-  const int kbase = st * TK;
+  const int kbase = k0 + st * TK;
 #pragma unroll
   for (int c = 0; c < (TM * TK / 8) / NT; c++) {
     const int chunk = threadIdx.x + c * NT;          // 0 .. 511
     const int r = chunk / (TK / 8), k8 = chunk % (TK / 8);   // row, 8-element segment
     const uint32_t off = (uint32_t)(((r >> 3) * (TK / 8) + k8) * 128 + (r & 7) * 16);
     const int kc = kbase + k8 * 8;
-    const bool vk = kc < g.K;
+    const bool vk = kc < kend;
     const int64_t ra = row0 + r;
     const bool va = vk && ra < g.M;
     cp_async16(smem_u32(sA + off), g.A + (va ? ra * g.lda + kc : 0), va);
@@ -130,11 +135,13 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const int nst = (g.K + TK - 1) / TK;   // K segments past K are zero-filled
+  const int k0 = blockIdx.z * g.kchunk;
+  const int kend = k0 + g.kchunk < g.K ? k0 + g.kchunk : g.K;
+  const int nst = kend > k0 ? (kend - k0 + TK - 1) / TK : 0;   // segments past kend are zero-filled
   // prologue: the first NS stages in flight
   int issued = 0;
   int committed = -1;   // the stage whose MMAs were committed last
-  for (; issued < NS && issued < nst; issued++) load_stage(g, smem + issued * kStageBytes, issued, row0, col0);
+  for (; issued < NS && issued < nst; issued++) load_stage(g, smem + issued * kStageBytes, issued, row0, col0, k0, kend);
   for (int st = 0; st < nst; st++) {
     const int b = st % NS;
     // stage st's copies done (later groups may stay pending)
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
       }
       __syncthreads();
       if (s_fail) break;
-      load_stage(g, smem + bp * kStageBytes, sp + NS, row0, col0);
+      load_stage(g, smem + bp * kStageBytes, sp + NS, row0, col0, k0, kend);
       issued++;
     }
   }
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (!s_fail) {
+  if (!s_fail && nst > 0) {
     // ---- epilogue.  The stage buffers are free now: the bias of the tile's
     // columns and one 32-column chunk of the accumulator at a time are
     // staged there, so that each warp can store its 32 rows with the lanes
@@ -222,8 +229,14 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
       for (int rr = 0; rr < 32; rr++) {
         const int64_t row = row0 + warp * 32 + rr;
         if (row < g.M && col < g.N) {
-          float x = stile[(warp * 32 + rr) * 33 + lane] + bcol;
+          float x = stile[(warp * 32 + rr) * 33 + lane];
+          if (g.accumulate) {
+            atomicAdd(&reinterpret_cast<float *>(g.C)[row * g.ldc + col], x);
+            continue;
+          }
+          x += bcol;
           if (g.relu) x = x > 0.0f ? x : 0.0f;
+          if (g.mask && !(__bfloat162float(g.mask[row * g.ldm + col]) > 0.0f)) x = 0.0f;
           if (g.out_bf16)
             reinterpret_cast<__nv_bfloat16 *>(g.C)[row * g.ldc + col] = __float2bfloat16(x);
           else
@@ -237,6 +250,26 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TN) : "memory");
+}
+
+// out [C][R] = in [R][C]^T (bf16, row-major; leading dimensions ldi, ldo),
+// through 32 x 32 shared-memory tiles.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *in, int64_t R, int C, int64_t ldi,
+                                      __nv_bfloat16 *out, int64_t ldo) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i;
+    const int c = c0 + threadIdx.x;
+    t[i][threadIdx.x] = (r < R && c < C) ? in[r * ldi + c] : __float2bfloat16(0.0f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i;
+    const int64_t r = r0 + threadIdx.x;
+    if (c < C && r < R) out[(int64_t)c * ldo + r] = t[threadIdx.x][i];
+  }
 }
 
 }  // namespace fem_mlp_tc
