@@ -25,7 +25,8 @@ int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
     return FEM_EINVAL;
   } else {
     auto kern = fem_apply_kernel<T, P, Q, KIND, COLLOC, EPB>;
-    static int max_bps = -1;
+    static FemKernelCache cache;
+    int &max_bps = cache.here();
     if (max_bps < 0) {
       FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
@@ -50,7 +51,8 @@ int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
   auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND>;
-  static int max_bps = -1;
+  static FemKernelCache cache;
+  int &max_bps = cache.here();
   if (max_bps < 0) {
     FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

@@ -103,6 +103,20 @@ struct fem_op {
 
 #define FEM_MAX_BLOCKS 8192
 
+// Per-device facts of one kernel that are set up at its first launch on a
+// device (the dynamic shared-memory attribute, the resident blocks per SM):
+// both belong to the current device, not to the process.
+constexpr int FEM_MAX_DEVICES = 64;
+struct FemKernelCache {
+  int v[FEM_MAX_DEVICES];
+  FemKernelCache() { for (int &x : v) x = -1; }
+  int &here() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return v[(d >= 0 && d < FEM_MAX_DEVICES) ? d : 0];
+  }
+};
+
 // Device table block of an operator: B [Q][P] | Dq [Q][Q] | G [Q][P] | w [Q]
 // at fixed offsets (FP64 and FP32 copies).
 #define TAB_B 0

@@ -174,11 +174,12 @@ int gemm(const fem_mlp *n, const GemmArgs &a, bool AT, bool BT) {
     kchunk = (kchunk + fem_mlp_tc::TK - 1) / fem_mlp_tc::TK * fem_mlp_tc::TK;
     ks = (a.K + kchunk - 1) / kchunk;
     t.kchunk = kchunk;
-    static bool attr = false;
-    if (!attr) {
+    static FemKernelCache attr;   // the attribute belongs to the current device
+    int &set = attr.here();
+    if (set < 0) {
       FEM_CUDA_TRY(cudaFuncSetAttribute(fem_mlp_tc::gemm_tc_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, fem_mlp_tc::kSmemBytes));
-      attr = true;
+      set = 1;
     }
     dim3 grid((unsigned)((a.M + fem_mlp_tc::TM - 1) / fem_mlp_tc::TM),
               (unsigned)((a.N + fem_mlp_tc::TN - 1) / fem_mlp_tc::TN), (unsigned)ks);
