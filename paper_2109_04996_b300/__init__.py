@@ -151,9 +151,27 @@ def _ptr(t):
     if t is None:
         return None
     if isinstance(t, np.ndarray):
-        assert t.flags["C_CONTIGUOUS"]
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("host array must be C-contiguous")
         return t.ctypes.data
-    assert t.is_contiguous()
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _vec(t, dtype, n, what="vector"):
+    """Device pointer of a contiguous CUDA tensor of `n` elements of `dtype`
+    (the library reads and writes exactly that many; anything else would
+    make it touch memory outside the tensor)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (what, dtype, t.dtype))
+    if t.numel() != n:
+        raise ValueError("%s must have %d elements, got %d" % (what, n, t.numel()))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
     return t.data_ptr()
 
 
@@ -208,9 +226,20 @@ class Mesh:
 
     def __init__(self, mesh, node_xyz=None, stream=None):
         self.p = int(mesh["p"]); self.N = int(mesh["N"]); self.E = int(mesh["E"])
+        P3 = (self.p + 1) ** 3
         en = np.ascontiguousarray(mesh["elem_nodes"], dtype=np.int32)
+        if en.size != self.E * P3:
+            raise ValueError("elem_nodes must hold E * (p+1)^3 = %d ids, got %d" % (self.E * P3, en.size))
         dr = mesh.get("dirichlet")
         dr = None if dr is None else np.ascontiguousarray(dr, dtype=np.uint8)
+        if dr is not None and dr.size != self.N:
+            raise ValueError("dirichlet must have N = %d entries, got %d" % (self.N, dr.size))
+        if node_xyz is None:
+            ev = np.asarray(mesh["elem_verts"])
+            if ev.shape != (self.E, 8) or np.asarray(mesh["vert_xyz"]).shape[1:] != (3,):
+                raise ValueError("elem_verts must be [E, 8] and vert_xyz [nvert, 3]")
+        elif np.asarray(node_xyz).size != 3 * self.N:
+            raise ValueError("node_xyz must be [N, 3]")
         self.dirichlet = dr
         h = _VP()
         if node_xyz is None:
@@ -279,28 +308,32 @@ class Operator:
         import torch
         if y is None:
             y = torch.empty_like(x)
-        _check(lib().fem_op_apply(self._h, _ptr(x), _ptr(y)))
+        _check(lib().fem_op_apply(self._h, _vec(x, torch.float64, self.n, "x"),
+                                  _vec(y, torch.float64, self.n, "y")))
         return y
 
     def apply_f32(self, x, y=None):
         import torch
         if y is None:
             y = torch.empty_like(x)
-        _check(lib().fem_op_apply_f32(self._h, _ptr(x), _ptr(y)))
+        _check(lib().fem_op_apply_f32(self._h, _vec(x, torch.float32, self.n, "x"),
+                                      _vec(y, torch.float32, self.n, "y")))
         return y
 
     def apply_elements(self, elems, x, y=None):
         import torch
         if y is None:
             y = torch.empty_like(x)
-        _check(lib().fem_op_apply_elements(self._h, _ptr(elems), elems.numel(), _ptr(x), _ptr(y)))
+        _check(lib().fem_op_apply_elements(self._h, _vec(elems, torch.int32, elems.numel(), "elems"),
+                                           elems.numel(), _vec(x, torch.float64, self.n, "x"),
+                                           _vec(y, torch.float64, self.n, "y")))
         return y
 
     def diagonal(self, d=None):
         import torch
         if d is None:
             d = torch.empty(self.n, dtype=torch.float64, device="cuda")
-        _check(lib().fem_op_diagonal(self._h, _ptr(d)))
+        _check(lib().fem_op_diagonal(self._h, _vec(d, torch.float64, self.n, "d")))
         return d
 
     def qdata(self, e):
@@ -313,7 +346,7 @@ class Operator:
         import torch
         if b is None:
             b = torch.empty(self.N, dtype=torch.float64, device="cuda")
-        _check(lib().fem_op_rhs(self._h, which, _ptr(b)))
+        _check(lib().fem_op_rhs(self._h, which, _vec(b, torch.float64, self.N, "b")))
         return b
 
     def cg(self, b, x, precond=PC_JACOBI, maxit=10000, rtol=1e-10, use_graph=True):
@@ -322,7 +355,9 @@ class Operator:
         on breakdown, returns status FEM_ENOCONV without raising."""
         o = _CgOpts(precond, int(maxit), float(rtol), 1 if use_graph else 0, 0.0, 0)
         st = _CgStats()
-        rc = lib().fem_cg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        import torch
+        rc = lib().fem_cg_solve(self._h, _vec(b, torch.float64, self.n, "b"),
+                                _vec(x, torch.float64, self.n, "x"), ctypes.byref(o), ctypes.byref(st))
         if rc not in (0, 5):
             _check(rc)
         return _stats(st)
@@ -332,7 +367,9 @@ class Operator:
         import torch
         if r is None:
             r = torch.empty_like(x)
-        _check(lib().fem_op_residual(self._h, _ptr(b), _ptr(x), _ptr(r)))
+        _check(lib().fem_op_residual(self._h, _vec(b, torch.float64, self.n, "b"),
+                                     _vec(x, torch.float64, self.n, "x"),
+                                     _vec(r, torch.float64, self.n, "r")))
         return r
 
     def set_launch_shape(self, prec, epb_choice, blocks_per_sm=0):
@@ -353,7 +390,10 @@ class Operator:
         created with prec=F32).  x: initial guess in, solution out."""
         o = _CgOpts(precond, int(maxit), float(rtol), 1, float(inner_rtol), int(max_outer))
         st = _CgStats()
-        rc = lib().fem_solve_refined(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        import torch
+        rc = lib().fem_solve_refined(self._h, _vec(b, torch.float64, self.n, "b"),
+                                     _vec(x, torch.float64, self.n, "x"), ctypes.byref(o),
+                                     ctypes.byref(st))
         if rc not in (0, 5):
             _check(rc)
         return _stats(st)
@@ -382,8 +422,12 @@ class Batch:
             self._h = None
 
     def _vecs(self, bs, xs):
-        assert len(bs) == len(self.ops) == len(xs)
-        return (_VP * len(bs))(*[_ptr(b) for b in bs]), (_VP * len(xs))(*[_ptr(x) for x in xs])
+        import torch
+        if not (len(bs) == len(self.ops) == len(xs)):
+            raise ValueError("one right-hand side and one solution per problem")
+        bp = [_vec(b, torch.float64, op.n, "b") for b, op in zip(bs, self.ops)]
+        xp = [_vec(x, torch.float64, op.n, "x") for x, op in zip(xs, self.ops)]
+        return (_VP * len(bs))(*bp), (_VP * len(xs))(*xp)
 
     def solve(self, bs, xs, rtol=1e-10, inner_rtol=0.1, maxit=100000, max_outer=100):
         o = _CgOpts(PC_JACOBI, int(maxit), float(rtol), 0, float(inner_rtol), int(max_outer))
@@ -439,30 +483,39 @@ class Mlp:
         _check(lib().fem_mlp_params(self._h, _ptr(out), ctypes.byref(n)))
         return out
 
+    def _xt(self, X, T=None):
+        """Pointers of X [S][n_in] (input dtype) and T [S][n_out] (fp32)."""
+        import torch
+        S = X.shape[0]
+        px = _vec(X, self.input_dtype, S * self.n_in, "X")
+        pt = None if T is None else _vec(T, torch.float32, S * self.n_out, "T")
+        return S, px, pt
+
     def forward(self, X):
         import torch
-        Y = torch.empty(X.shape[0], self.n_out, dtype=torch.float32, device=X.device)
-        _check(lib().fem_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Y)))
+        S, px, _ = self._xt(X)
+        Y = torch.empty(S, self.n_out, dtype=torch.float32, device=X.device)
+        _check(lib().fem_mlp_forward(self._h, px, S, _ptr(Y)))
         return Y
 
     def gradient(self, X, T, valid):
         """(loss, FP32 gradient) without updating."""
         g = np.zeros(self.params().size, dtype=np.float32)
         L = ctypes.c_double()
-        _check(lib().fem_mlp_train_step(self._h, _ptr(X), _ptr(T), X.shape[0], valid, 0.0,
-                                        _ptr(g), ctypes.byref(L)))
+        S, px, pt = self._xt(X, T)
+        _check(lib().fem_mlp_train_step(self._h, px, pt, S, valid, 0.0, _ptr(g), ctypes.byref(L)))
         return L.value, g
 
     def step(self, X, T, valid, lr):
         L = ctypes.c_double()
-        _check(lib().fem_mlp_train_step(self._h, _ptr(X), _ptr(T), X.shape[0], valid, lr, None,
-                                        ctypes.byref(L)))
+        S, px, pt = self._xt(X, T)
+        _check(lib().fem_mlp_train_step(self._h, px, pt, S, valid, lr, None, ctypes.byref(L)))
         return L.value
 
     def train(self, X, T, valid, epochs, batch=4096, lr=1e-3, seed=0):
         losses = np.zeros(epochs)
-        _check(lib().fem_mlp_train(self._h, _ptr(X), _ptr(T), X.shape[0], valid, epochs, batch,
-                                   lr, seed, _ptr(losses)))
+        S, px, pt = self._xt(X, T)
+        _check(lib().fem_mlp_train(self._h, px, pt, S, valid, epochs, batch, lr, seed, _ptr(losses)))
         return losses
 
 
@@ -487,8 +540,14 @@ class Precond:
         return out
 
     def samples(self, b, x_star, x_k, X, T):
-        _check(lib().fem_precond_samples(self._h, _ptr(b), _ptr(x_star), _ptr(x_k), _ptr(X),
-                                         _ptr(T)))
+        import torch
+        n, E = self.op.n, self.op.E
+        if self.mlp is None:
+            raise ValueError("samples need a network")
+        _check(lib().fem_precond_samples(
+            self._h, _vec(b, torch.float64, n, "b"), _vec(x_star, torch.float64, n, "x_star"),
+            _vec(x_k, torch.float64, n, "x_k"), _vec(X, self.mlp.input_dtype, E * self.mlp.n_in, "X"),
+            _vec(T, torch.float32, E * self.mlp.n_out, "T")))
 
     def set_gamma(self, gamma):
         _check(lib().fem_precond_set_gamma(self._h, float(gamma)))
@@ -513,13 +572,16 @@ class Precond:
     def apply(self, r):
         import torch
         z = torch.empty_like(r)
-        _check(lib().fem_precond_apply(self._h, _ptr(r), _ptr(z)))
+        _check(lib().fem_precond_apply(self._h, _vec(r, torch.float32, self.op.n, "r"),
+                                       _vec(z, torch.float32, self.op.n, "z")))
         return z
 
     def fcg(self, b, x, rtol=1e-10, inner_rtol=0.1, maxit=100000, max_outer=100):
         o = _CgOpts(PC_LEARNED, int(maxit), float(rtol), 1, float(inner_rtol), int(max_outer))
         st = _CgStats()
-        rc = lib().fem_fcg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        import torch
+        rc = lib().fem_fcg_solve(self._h, _vec(b, torch.float64, self.op.n, "b"),
+                                 _vec(x, torch.float64, self.op.n, "x"), ctypes.byref(o), ctypes.byref(st))
         if rc not in (0, 5):
             _check(rc)
         return _stats(st)
@@ -558,25 +620,33 @@ class Pmg:
     def prolong(self, level, xc):
         import torch
         xf = torch.empty(self.levels[level].n, dtype=torch.float64, device=xc.device)
-        _check(lib().fem_pmg_prolong(self._h, int(level), _ptr(xc), _ptr(xf)))
+        _check(lib().fem_pmg_prolong(self._h, int(level),
+                                     _vec(xc, torch.float64, self.levels[level + 1].n, "xc"),
+                                     _vec(xf, torch.float64, self.levels[level].n, "xf")))
         return xf
 
     def restrict(self, level, rf):
         import torch
         rc = torch.empty(self.levels[level + 1].n, dtype=torch.float64, device=rf.device)
-        _check(lib().fem_pmg_restrict(self._h, int(level), _ptr(rf), _ptr(rc)))
+        _check(lib().fem_pmg_restrict(self._h, int(level),
+                                      _vec(rf, torch.float64, self.levels[level].n, "rf"),
+                                      _vec(rc, torch.float64, self.levels[level + 1].n, "rc")))
         return rc
 
     def vcycle(self, r):
         import torch
         z = torch.empty_like(r)
-        _check(lib().fem_pmg_vcycle(self._h, _ptr(r), _ptr(z)))
+        _check(lib().fem_pmg_vcycle(self._h, _vec(r, torch.float64, self.levels[0].n, "r"),
+                                    _vec(z, torch.float64, self.levels[0].n, "z")))
         return z
 
     def solve(self, b, x, rtol=1e-10, maxit=1000):
         o = _CgOpts(0, int(maxit), float(rtol), 1, 0.0, 0)
         st = _CgStats()
-        rc = lib().fem_pmg_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st))
+        import torch
+        n = self.levels[0].n
+        rc = lib().fem_pmg_solve(self._h, _vec(b, torch.float64, n, "b"), _vec(x, torch.float64, n, "x"),
+                                 ctypes.byref(o), ctypes.byref(st))
         if rc not in (0, 5):
             _check(rc)
         return _stats(st)

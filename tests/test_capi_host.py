@@ -93,3 +93,23 @@ def test_pmg_create_rejects_bad_hierarchies_without_a_gpu(L):
     assert b"level 0" in L.fem_last_error()
     assert L.fem_pmg_vcycle(None, None, None) == 1
     assert L.fem_pmg_solve(None, None, None, None, None) == 1
+
+
+def test_binding_validates_buffers_before_the_library_sees_them():
+    import torch
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        fem._vec(torch.zeros(8, dtype=torch.float64), torch.float64, 8)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        fem._vec(np.zeros(8), torch.float64, 8)
+    with pytest.raises(ValueError, match="contiguous"):
+        fem._ptr(np.zeros((4, 4))[:, 1])
+    m = fem_inputs.box_mesh(2, 2)
+    bad = dict(m, elem_nodes=m["elem_nodes"][:-1])
+    with pytest.raises(ValueError, match="elem_nodes"):
+        fem.Mesh(bad)
+    bad = dict(m, dirichlet=m["dirichlet"][:-3])
+    with pytest.raises(ValueError, match="dirichlet"):
+        fem.Mesh(bad)
+    bad = dict(m, elem_verts=m["elem_verts"][:, :7])
+    with pytest.raises(ValueError, match="elem_verts"):
+        fem.Mesh(bad)
