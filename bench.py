@@ -769,13 +769,32 @@ def main():
     hx = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True)
           for (_, _, _, _, b, _) in ops]
 
+    # the copies run on their own stream: order k+1's right-hand side goes
+    # in and order k-1's solution comes out while order k solves (every copy
+    # stays inside the timed region)
+    cstream = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in ops]
+    ev_out = [torch.cuda.Event() for _ in ops]
+
+    def put_rhs(k):
+        with torch.cuda.stream(cstream):
+            ops[k][4].copy_(hb[k], non_blocking=True)
+            ev_in[k].record(cstream)
+
     def step_e2e():
+        put_rhs(0)
         for k, (p, n, gm, op, b, x) in enumerate(ops):
-            b.copy_(hb[k], non_blocking=True)
+            stream.wait_event(ev_in[k])
+            if k + 1 < len(ops):
+                put_rhs(k + 1)
             x.zero_()
             op.cg(b, x, precond=fem.PC_JACOBI, maxit=args.iters, rtol=0.0, use_graph=True)
-            hx[k].copy_(x, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+            ev_out[k].record(stream)
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(ev_out[k])
+                hx[k].copy_(x, non_blocking=True)
+        cstream.synchronize()
+        stream.synchronize()
 
     step_e2e()
     torch.cuda.synchronize()
