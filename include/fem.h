@@ -194,12 +194,16 @@ fem_status fem_op_rhs(fem_op *op, int which, double *b);
 /* ---------------------------------------------------------------- autotuning */
 
 /* Launch shape of the fused apply.  epb_choice selects the element body and
- * the elements per block: for diffusion 0, 1, 2 = the line-based body with
- * even-odd split 1D operators and about 256, 128 or 512 threads per block,
- * 3, 4, 5 = the slab body (one thread per quadrature column) with the same
- * three sizes; for mass 0, 1, 2 = the slab body (only 0 when collocated).
+ * the elements per block: 0, 1, 2 = the line-based body with even-odd split
+ * 1D operators and about 256, 128 or 512 threads per block, 3, 4, 5 = the
+ * slab body (one thread per quadrature column) with the same three sizes,
+ * 6 = the trilinear body (one thread per element; Gauss diffusion at p = 1
+ * only).  The collocated mass operator (pointwise) has choice 0 only.
  * blocks_per_sm: resident blocks per SM (0 = the occupancy maximum).
- * Defaults: diffusion FP32 0; FP64 0 for Gauss with q >= 8, else 3. */
+ * Defaults (measured): FP64 diffusion 6 at p = 1 (Gauss), 3 for p = 2 and
+ * the collocated operators, 0 from q = 5; FP32 diffusion 0, except p = 1
+ * Gauss (6 with 2 blocks per SM at q = 3, 4 at q = 2); non-collocated mass
+ * FP32 1, FP64 3 below q = 5, 0 up to q = 8, 1 from q = 9. */
 typedef struct {
   int epb_choice;
   int blocks_per_sm;
@@ -236,6 +240,9 @@ typedef struct {
   double inner_rtol;  /* fem_solve_refined: relative tolerance of each inner
                          FP32 solve */
   int max_outer;      /* fem_solve_refined: outer FP64 refinement steps cap */
+  int zero_guess;     /* fem_cg_solve: 1 = start from x = 0 (x's entries on
+                         entry are ignored; the initial residual is b and no
+                         apply is spent on it), 0 = x is the initial guess */
 } fem_cg_opts;
 
 typedef struct {
@@ -253,7 +260,8 @@ typedef struct {
  * preconditioner as in Nekbone, section "Miniapps") on the Dirichlet-
  * constrained system  (M A M + (I - M)) x = b,  M = interior mask, FP64 apply.
  * b, x: device [ncomp*N]; x is the initial guess on entry (its Dirichlet
- * entries are set to 0) and the solution on exit.  Scalars stay on the
+ * entries are set to 0; opts->zero_guess = 1 starts from 0 instead) and the
+ * solution on exit.  Scalars stay on the
  * device; with use_graph = 1 the whole loop is one graph launch.  Copies the
  * statistics back (synchronizes).  Returns FEM_OK, FEM_ENOCONV (maxit reached
  * with rtol > 0) or FEM_EBREAKDOWN. */
@@ -287,7 +295,7 @@ fem_status fem_op_residual(fem_op *op, const double *b, const double *x,
  * x in R^n_in, hidden width n_h, y in R^n_out (all multiples of 32).
  * Parameters: one FP32 array in the order W1 [n_h][n_in], b1, W2 [n_h][n_h],
  * b2, W3 [n_out][n_h], b3 (FP32 masters, Adam moments on the device).
- * mode 0: GEMMs in bf16 on the tensor cores (mma.sync) with FP32
+ * mode 0: GEMMs in bf16 on the tensor cores (tcgen05) with FP32
  * accumulation, activations in bf16; mode 1: all FP32 (reference/debug).
  * Row inputs X are bf16 (mode 0) or FP32 (mode 1), row-major [rows][n_in]. */
 typedef struct fem_mlp fem_mlp;

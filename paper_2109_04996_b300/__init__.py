@@ -45,7 +45,7 @@ class _TuneResult(ctypes.Structure):
 class _CgOpts(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int), ("maxit", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("use_graph", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("max_outer", ctypes.c_int)]
+                ("max_outer", ctypes.c_int), ("zero_guess", ctypes.c_int)]
 
 
 class _CgStats(ctypes.Structure):
@@ -349,11 +349,15 @@ class Operator:
         _check(lib().fem_op_rhs(self._h, which, _vec(b, torch.float64, self.N, "b")))
         return b
 
-    def cg(self, b, x, precond=PC_JACOBI, maxit=10000, rtol=1e-10, use_graph=True):
+    def cg(self, b, x, precond=PC_JACOBI, maxit=10000, rtol=1e-10, use_graph=True,
+           zero_guess=False):
         """Solve the Dirichlet-constrained system in place (x: initial guess
-        in, solution out).  Returns the statistics as a dict; raises FemError
-        on breakdown, returns status FEM_ENOCONV without raising."""
-        o = _CgOpts(precond, int(maxit), float(rtol), 1 if use_graph else 0, 0.0, 0)
+        in, solution out; zero_guess=True starts from 0 whatever x holds and
+        skips the initial residual's apply).  Returns the statistics as a
+        dict; raises FemError on breakdown, returns status FEM_ENOCONV without
+        raising."""
+        o = _CgOpts(precond, int(maxit), float(rtol), 1 if use_graph else 0, 0.0, 0,
+                    1 if zero_guess else 0)
         st = _CgStats()
         import torch
         rc = lib().fem_cg_solve(self._h, _vec(b, torch.float64, self.n, "b"),

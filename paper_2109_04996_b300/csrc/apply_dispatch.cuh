@@ -4,6 +4,7 @@
 // apply_f32.cu).
 #pragma once
 #include "apply_lines.cuh"
+#include "apply_trilinear.cuh"
 
 namespace fem_apply {
 
@@ -97,11 +98,45 @@ int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
   }
 }
 
+// Trilinear diffusion (p = 1, Gauss): one thread per element.
+template <typename T, int Q>
+int launch_trilinear(fem_op *op, const ApplyParams<T> &prm, int bps) {
+  TrilinearParams<T, Q> tp;
+  tp.a = prm;
+  for (int k = 0; k < Q; k++)
+    for (int a = 0; a < 2; a++) {
+      tp.t.B[k][a] = (T)op->tab.B[k * 2 + a];
+      tp.t.H[k][a] = (T)(0.5 * op->tab.B[k * 2 + a]);
+    }
+  constexpr int NT = kTrilinearThreads;
+  auto kern = fem_apply_trilinear_kernel<T, Q>;
+  static FemKernelCache cache;
+  int &max_bps = cache.here();
+  if (max_bps < 0) {
+    int per_sm = 0;
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0));
+    max_bps = per_sm < 1 ? 1 : per_sm;
+  }
+  const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
+  const int64_t nblk = (prm.nsel + NT - 1) / NT;
+  int64_t grid = (int64_t)op->nsm * use;
+  if (grid > nblk) grid = nblk;
+  if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, NT, 0, op->stream()>>>(tp);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
 // Launch shape choice: 0..2 the line-based body with the three EPB
-// candidates, 3..5 the slab body; the collocated mass operator (pointwise)
-// has only the slab body.
+// candidates, 3..5 the slab body, 6 the trilinear body (Gauss diffusion at
+// p = 1 only); the collocated mass operator (pointwise) has only the slab
+// body.
 template <typename T, int P, int Q, int KIND, bool COLLOC>
 int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
+  if constexpr (P == 2 && KIND == FEM_DIFFUSION && !COLLOC) {
+    if (choice == 6) return launch_trilinear<T, Q>(op, prm, bps);
+  }
   if constexpr (KIND == FEM_DIFFUSION || !COLLOC) {
     switch (choice) {
       case 0: return launch_lines<T, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps);
@@ -155,9 +190,5 @@ int dispatch(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
   return FEM_EINVAL;
 }
 
-// Number of launch shape choices for this operator.
-inline int epb_choices(const fem_op *op) {
-  return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
-}
 
 }  // namespace fem_apply

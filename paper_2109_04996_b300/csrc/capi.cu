@@ -222,6 +222,14 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
     // block, 3.4 vs 3.0 GDOF/s for the line body)
     op->tune_epb[FEM_F32] = (!op->colloc && Q == 3) ? 4 : 0;
     op->tune_epb[FEM_F64] = (!op->colloc && Q >= 5) ? 0 : 3;
+    if (!op->colloc && P == 2) {
+      // trilinear Gauss diffusion (8e6 DOFs): the thread-per-element body in
+      // FP64 (q = 3: 2.4x the slab body, q = 2: 1.3x) and in FP32 at q = 3
+      // with two blocks per SM (1.13x); FP32 at q = 2 keeps the slab body
+      op->tune_epb[FEM_F64] = 6;
+      if (Q == 3) { op->tune_epb[FEM_F32] = 6; op->tune_bps[FEM_F32] = 2; }
+      else op->tune_epb[FEM_F32] = 4;
+    }
   } else if (!op->colloc) {
     // mass (BP1 at 8e6 DOFs): FP32 line body with half the default elements
     // per block (2.4-3.2x the slab body for p >= 4); FP64 line body from

@@ -30,6 +30,7 @@ struct CgWork {
   cudaGraphExec_t exec = nullptr;
   const double *g_b = nullptr;
   double *g_x = nullptr;
+  int g_zero = 0;                 // the graph's prologue starts from x = 0
 };
 
 namespace {
@@ -53,12 +54,12 @@ __global__ void cg_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N
   }
 }
 
-// x <- M x (Dirichlet entries to 0), y <- 0
+// x <- M x (Dirichlet entries to 0; every entry with zero = 1), y <- 0
 __global__ void cg_prepare_kernel(double *x, double *y, const uint8_t *dir, int64_t N,
-                                  int64_t n) {
+                                  int64_t n, int zero) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (dir && dir[i % N]) x[i] = 0.0;
+    if (zero || (dir && dir[i % N])) x[i] = 0.0;
     y[i] = 0.0;
   }
 }
@@ -189,14 +190,17 @@ CgParams make_params(fem_op *op, const double *b, double *x, cudaGraphConditiona
   return c;
 }
 
-// The launches of one solve before the loop.
-int launch_prologue(fem_op *op, const CgParams &c, cudaStream_t s) {
+// The launches of one solve before the loop.  zero_guess: x = 0, so A x = 0
+// (y stays zero) and no apply is needed for the initial residual.
+int launch_prologue(fem_op *op, const CgParams &c, cudaStream_t s, int zero_guess = 0) {
   const int g = grid_for(c.n);
-  cg_prepare_kernel<<<g, kThreads, 0, s>>>(c.x, c.y, c.dir, c.N, c.n);
+  cg_prepare_kernel<<<g, kThreads, 0, s>>>(c.x, c.y, c.dir, c.N, c.n, zero_guess);
   FEM_CHECK_LAUNCH();
-  // the apply launcher uses the operator's stream; route it to s
-  int rc = fem_launch_apply_f64(op, c.x, c.y, nullptr, op->E, nullptr);
-  if (rc) return rc;
+  if (!zero_guess) {
+    // the apply launcher uses the operator's stream; route it to s
+    int rc = fem_launch_apply_f64(op, c.x, c.y, nullptr, op->E, nullptr);
+    if (rc) return rc;
+  }
   cg_init_kernel<<<g, kThreads, 0, s>>>(c);
   FEM_CHECK_LAUNCH();
   return FEM_OK;
@@ -224,7 +228,7 @@ void destroy_graph(CgWork *w) {
 // Streams used while capturing: the apply launcher enqueues on
 // op->stream(), so capture happens on the operator's own stream (mesh stream
 // swapped for the duration of the capture).
-static int build_graph(fem_op *op, const double *b, double *x) {
+static int build_graph(fem_op *op, const double *b, double *x, int zero_guess) {
   CgWork *w = op->cg;
   destroy_graph(w);
   fem_mesh *mesh = const_cast<fem_mesh *>(op->mesh);
@@ -250,7 +254,7 @@ static int build_graph(fem_op *op, const double *b, double *x) {
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
     c = make_params(op, b, x, h, 1);
-    rc = launch_prologue(op, c, w->cap);
+    rc = launch_prologue(op, c, w->cap, zero_guess);
     if (rc) goto end_capture;
     e = cudaStreamGetCaptureInfo(w->cap, &st, nullptr, &graph, &deps, nullptr, &ndeps);
     if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
@@ -288,7 +292,7 @@ end_capture : {
   w->graph = g2;
 }
   FEM_CUDA_TRY(cudaGraphInstantiate(&w->exec, w->graph, 0));
-  w->g_b = b; w->g_x = x;
+  w->g_b = b; w->g_x = x; w->g_zero = zero_guess;
   return FEM_OK;
 }
 
@@ -309,16 +313,17 @@ int fem_cg_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
   init.tol2 = o->rtol * o->rtol;
   FEM_CUDA_TRY(cudaMemcpyAsync(w->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   if (o->use_graph) {
-    if (!w->exec || w->g_b != b || w->g_x != x) {
+    const int zero = o->zero_guess ? 1 : 0;
+    if (!w->exec || w->g_b != b || w->g_x != x || w->g_zero != zero) {
       // the capture streams must see the work queued so far on s
       FEM_CUDA_TRY(cudaStreamSynchronize(s));
-      rc = build_graph(op, b, x);
+      rc = build_graph(op, b, x, zero);
       if (rc) return rc;
     }
     FEM_CUDA_TRY(cudaGraphLaunch(w->exec, s));
   } else {
     CgParams c = make_params(op, b, x, 0, 0);
-    rc = launch_prologue(op, c, s);
+    rc = launch_prologue(op, c, s, o->zero_guess ? 1 : 0);
     if (rc) return rc;
     for (int it = 0; it < o->maxit; it++) {
       rc = launch_body(op, c, s);

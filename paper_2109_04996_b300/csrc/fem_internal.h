@@ -130,11 +130,20 @@ int fem_launch_apply_f64(fem_op *op, const double *x, double *y,
                          const int32_t *list, int64_t nsel, double *dot_out);
 int fem_launch_apply_f32(fem_op *op, const float *x, float *y,
                          const int32_t *list, int64_t nsel, double *dot_out);
-// explicit launch shape (autotuner): EPB choice index 0..2, blocks per SM (0 = max)
+// explicit launch shape (autotuner): body / elements-per-block choice
+// (fem_apply_choices), blocks per SM (0 = max)
 int fem_launch_apply_f64_shape(fem_op *op, const double *x, double *y, const int32_t *list,
                                int64_t nsel, double *dot_out, int choice, int bps);
 int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32_t *list,
                                int64_t nsel, double *dot_out, int choice, int bps);
+// Launch shape choices of an operator's apply: 0..2 the line-based body
+// (elements per block default, half, double), 3..5 the slab body, 6 the
+// trilinear body (Gauss diffusion at p = 1); the collocated mass operator
+// (pointwise) has one.
+inline int fem_apply_choices(const fem_op *op) {
+  if (op->kind == FEM_DIFFUSION && !op->colloc && op->P == 2) return 7;
+  return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
+}
 // ---- setup (setup.cu)
 int fem_setup_qdata(fem_op *op);
 int fem_setup_diagonal(fem_op *op);

@@ -9,7 +9,7 @@
 //   z = dinv * r + sum_e G_e^T (w_e * c_e),  w_e = 1 / node multiplicity.
 //
 // Weights are FP32 masters; the GEMMs run in bf16 with FP32 accumulation
-// (mma.sync), or in FP32 in the debug mode.  Training: mean squared error
+// (tcgen05 tensor cores, mlp_tc.cuh), or in FP32 in the debug mode.  Training: mean squared error
 // against e_e / ||r_e|| for residual/error pairs of the plain solver, Adam.
 #include <math.h>
 #include <string.h>
@@ -127,7 +127,7 @@ int gemm(const fem_mlp *n, const GemmArgs &a, bool AT, bool BT) {
     fem_set_error("mlp gemm: K=%d (split %d) / leading dimensions not multiples of 32 / 8", a.K, a.ksplit);
     return FEM_EINVAL;
   }
-  if (n->mode == 0 && !(AT && !BT)) {
+  if (n->mode == 0) {
     // tcgen05 tensor cores.  The kernel takes both operands K-major; an
     // operand stored the other way ([K][M] or [K][N]: the backward products)
     // is first transposed into a scratch copy.
@@ -187,19 +187,12 @@ int gemm(const fem_mlp *n, const GemmArgs &a, bool AT, bool BT) {
     FEM_CHECK_LAUNCH();
     return FEM_OK;
   }
-  if (n->mode == 0) {
-    dim3 grid((unsigned)((a.M + 127) / 128), (unsigned)((a.N + 127) / 128), (unsigned)a.ksplit);
-    if (!AT && !BT) fem_mlp_k::gemm_bf16_kernel<false, false><<<grid, 256, 0, s>>>(a);
-    else if (!AT && BT) fem_mlp_k::gemm_bf16_kernel<false, true><<<grid, 256, 0, s>>>(a);
-    else if (AT && BT) fem_mlp_k::gemm_bf16_kernel<true, true><<<grid, 256, 0, s>>>(a);
-    else fem_mlp_k::gemm_bf16_kernel<true, false><<<grid, 256, 0, s>>>(a);
-  } else {
-    dim3 grid((unsigned)((a.M + 63) / 64), (unsigned)((a.N + 63) / 64), (unsigned)a.ksplit);
-    if (!AT && !BT) fem_mlp_k::gemm_f32_kernel<false, false><<<grid, 256, 0, s>>>(a);
-    else if (!AT && BT) fem_mlp_k::gemm_f32_kernel<false, true><<<grid, 256, 0, s>>>(a);
-    else if (AT && BT) fem_mlp_k::gemm_f32_kernel<true, true><<<grid, 256, 0, s>>>(a);
-    else fem_mlp_k::gemm_f32_kernel<true, false><<<grid, 256, 0, s>>>(a);
-  }
+  // mode 1: the FP32 debug network
+  dim3 grid((unsigned)((a.M + 63) / 64), (unsigned)((a.N + 63) / 64), (unsigned)a.ksplit);
+  if (!AT && !BT) fem_mlp_k::gemm_f32_kernel<false, false><<<grid, 256, 0, s>>>(a);
+  else if (!AT && BT) fem_mlp_k::gemm_f32_kernel<false, true><<<grid, 256, 0, s>>>(a);
+  else if (AT && BT) fem_mlp_k::gemm_f32_kernel<true, true><<<grid, 256, 0, s>>>(a);
+  else fem_mlp_k::gemm_f32_kernel<true, false><<<grid, 256, 0, s>>>(a);
   FEM_CHECK_LAUNCH();
   return FEM_OK;
 }

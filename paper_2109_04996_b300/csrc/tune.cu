@@ -16,11 +16,7 @@ namespace {
 
 const int kBpsCandidates[] = {1, 2, 3, 4, 6, 0};  // 0 = occupancy maximum
 
-// 0..2: line-based body (EPB default, half, double); 3..5: slab body;
-// the collocated mass operator (pointwise) has the slab body only
-int n_choices(const fem_op *op) {
-  return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
-}
+int n_choices(const fem_op *op) { return fem_apply_choices(op); }
 
 std::string cache_key(const fem_op *op, int prec) {
   int dev = 0, major = 0, minor = 0;

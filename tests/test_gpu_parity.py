@@ -184,3 +184,74 @@ def test_cg_restart_from_iterate_continues_the_solve():
     assert st2["rnorm"] <= 1e-10 * st2["bnorm"] * 1.0000001
     xr, _, _ = oracle.pcg(orc, b.cpu().numpy(), m["dirichlet"], rtol=1e-12)
     assert rel(x.cpu().numpy(), xr) <= 1e-8
+
+
+# ---------------------------------------------------------------- trilinear body
+
+@pytest.mark.parametrize("q", [2, 3])
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_trilinear_body_matches_oracle(q, ncomp):
+    # p = 1 Gauss diffusion, thread-per-element body (launch choice 6): 9^3
+    # elements = 6 blocks of 128 threads with a ragged tail, shuffled order
+    m = fem_inputs.box_mesh(9, 1, perturb=0.1, seed=12, shuffle_seed=4)
+    gm = fem.Mesh(m)
+    op = fem.Operator(gm, fem.DIFFUSION, fem.GAUSS, q, ncomp=ncomp, prec=fem.F32)
+    orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, q, ncomp=ncomp)
+    for prec, tol in ((fem.F64, TOL64), (fem.F32, 1e-5)):
+        for bps in (1, 0):
+            op.set_launch_shape(prec, 6, bps)
+            for x in inputs(m, ncomp, seed=q):
+                xt = torch.from_numpy(x).cuda()
+                if prec == fem.F64:
+                    y = op.apply(xt).cpu().numpy()
+                else:
+                    y = op.apply_f32(xt.float()).double().cpu().numpy()
+                assert rel(y, orc.apply(x)) <= tol, (prec, bps)
+    # a listed subset of elements, and the empty list
+    op.set_launch_shape(fem.F64, 6, 0)
+    x = inputs(m, ncomp)[0]
+    sel = np.random.default_rng(2).choice(m["E"], size=300, replace=False).astype(np.int32)
+    y = op.apply_elements(torch.from_numpy(sel).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, orc.apply(x, elems=sel)) <= TOL64
+    y0 = op.apply_elements(torch.zeros(0, dtype=torch.int32, device="cuda"),
+                           torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.all(y0 == 0.0)
+
+
+def test_trilinear_body_in_cg_and_only_where_valid():
+    # the fused p^T A p of the trilinear body drives CG to the oracle's count
+    m, gm, op, orc = make("BP3", 7, 1, shuffle=5)
+    op.set_launch_shape(fem.F64, 6, 0)
+    b = fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=4)
+    xr, itr, _ = oracle.pcg(orc, b, m["dirichlet"], rtol=1e-10)
+    x = torch.zeros(m["N"], dtype=torch.float64, device="cuda")
+    st = op.cg(torch.from_numpy(b).cuda(), x, precond=fem.PC_JACOBI, rtol=1e-10)
+    assert st["status"] == "FEM_OK" and abs(st["iterations"] - itr) <= 2
+    assert rel(x.cpu().numpy(), xr) <= 1e-8
+    # choice 6 exists for Gauss diffusion at p = 1 only
+    for name, p in (("BP3", 2), ("BP5", 1), ("BP1", 1)):
+        _, _, op2, _ = make(name, 2, p)
+        with pytest.raises(fem.FemError):
+            op2.set_launch_shape(fem.F64, 6, 0)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_cg_zero_guess_ignores_x_and_matches_explicit_zero(use_graph):
+    m, gm, op, orc = make("BP3", 4, 2, seed=6)
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=9)).cuda()
+    x0 = torch.zeros(m["N"], dtype=torch.float64, device="cuda")
+    st0 = op.cg(b, x0, rtol=1e-10, use_graph=use_graph)
+    # garbage in x, zero_guess: the same solve as from an explicit zero
+    x1 = torch.full_like(x0, 7.5)
+    st1 = op.cg(b, x1, rtol=1e-10, use_graph=use_graph, zero_guess=True)
+    assert st1["status"] == "FEM_OK" and abs(st1["iterations"] - st0["iterations"]) <= 1
+    assert rel(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-9
+    # fixed iteration count from zero: the oracle's iterate after 5 steps
+    xr, _, _ = oracle.pcg(orc, b.cpu().numpy(), m["dirichlet"], rtol=0.0, maxit=5)
+    x1.fill_(-3.0)
+    st = op.cg(b, x1, rtol=0.0, maxit=5, use_graph=use_graph, zero_guess=True)
+    assert st["iterations"] == 5 and rel(x1.cpu().numpy(), xr) <= 1e-10
+    # the same buffers without the flag again: x is the initial guess once more
+    st2 = op.cg(b, x1, rtol=1e-10, use_graph=use_graph)
+    assert st2["iterations"] < st0["iterations"]
+    assert rel(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-8

@@ -42,7 +42,9 @@ def test_every_launch_shape_matches_oracle(name, p, n, prec):
     x = np.random.default_rng(1).uniform(-1, 1, m["N"])
     ref = orc.apply(x)
     tol = 1e-12 if prec == fem.F64 else 1e-5
-    for choice in range(6):   # 0-2 line-based body, 3-5 slab body
+    # 0-2 line-based body, 3-5 slab body, 6 trilinear body (Gauss diffusion, p = 1)
+    nchoice = 7 if (p == 1 and kind == fem.DIFFUSION) else 6
+    for choice in range(nchoice):
         for bps in (1, 2, 0):
             op.set_launch_shape(prec, choice, bps)
             if prec == fem.F64:
