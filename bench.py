@@ -493,9 +493,11 @@ def section_suite(fem, torch, args):
 
 def _batched_mix(fem, torch, specs):
     """One batch of independent BP3 problems: FP32 operators with FP64
-    refinement, all inner iterations in one persistent kernel per outer
-    step, autotuned block shape; vs the same problems solved one after
-    another with fem_solve_refined (graphs warmed first)."""
+    refinement; problems of at least 2^21 unknowns solved alone with their
+    order-specialized kernels, the inner iterations of all others in one
+    persistent kernel per outer step (autotuned block shape); vs the same
+    problems solved one after another with fem_solve_refined (graphs warmed
+    first)."""
     probs = []
     for s_ in specs:
         m = fem_inputs.box_mesh(s_["n"], s_["p"], perturb=0.1, seed=s_["mesh_seed"])
@@ -537,6 +539,8 @@ def _batched_mix(fem, torch, specs):
             "seconds": best, "gdofs_per_cg_iteration": dof_it / best / 1e9,
             "max_true_rel_residual": worst, "all_converged": all(r["status"] == "FEM_OK" for r in res),
             "autotune": dict(tune, seconds=t_tune),
+            "solo_dofs": batch.solo_dofs, "solo_problems": len(batch.solo),
+            "solo_share_of_dofs": sum(probs[i][1].N for i in batch.solo) / sum(q[1].N for q in probs),
             "sequential_refined_seconds": seq, "speedup_vs_sequential": seq / best}
 
 

@@ -366,8 +366,16 @@ typedef struct fem_batch fem_batch;
  * operator with Gauss q = p+2 (BP3/BP4 type, any order and size) created
  * with FEM_F32, all on one stream.  The batch keeps pointers to the
  * operators (they must outlive it) and allocates the per-problem inner
- * vectors. */
+ * vectors.  fem_batch_create_split: problems with ncomp*N >= solo_dofs are
+ * not put in the persistent kernel but solved one after another by
+ * fem_solve_refined, whose order-specialized kernels run a large problem
+ * faster than the persistent kernel's all-orders body; solo_dofs <= 0 puts
+ * every problem in the persistent kernel.  fem_batch_create uses
+ * FEM_BATCH_SOLO_DOFS. */
+#define FEM_BATCH_SOLO_DOFS (1LL << 21)
 fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **out);
+fem_status fem_batch_create_split(fem_op *const *ops, int n, int64_t solo_dofs,
+                                  fem_batch **out);
 fem_status fem_batch_destroy(fem_batch *batch);
 
 /* Solve every problem i: (M A_i M + (I - M)) x_i = b_i with the method of
@@ -375,7 +383,8 @@ fem_status fem_batch_destroy(fem_batch *batch);
  * problems in lockstep outer steps; the inner iterations of all problems of
  * one outer step run in ONE persistent cooperative kernel (work items:
  * (problem, element group) and (problem, vector chunk); grid barriers with a
- * wall-clock limit).  b, x: host arrays of n device pointers.  opts: precond
+ * wall-clock limit).  Problems split off at creation are solved first, one
+ * after another.  b, x: host arrays of n device pointers.  opts: precond
  * must be FEM_PC_JACOBI; rtol, inner_rtol, maxit (inner cap per step),
  * max_outer as in fem_solve_refined.  stats: host array of n (or NULL).
  * Returns the first non-OK problem status, or FEM_ETIMEOUT if a barrier ran
@@ -386,7 +395,8 @@ fem_status fem_batch_solve(fem_batch *batch, const double *const *b,
 
 /* Launch shape of the persistent kernel: block size choice (0: 128, 1: 256,
  * 2: 512 threads), blocks per SM (0 = occupancy maximum) and the barrier
- * wall-clock limit in ms. */
+ * wall-clock limit in ms.  (A batch whose problems are all split off has
+ * no persistent kernel: set_shape and autotune then do nothing.) */
 fem_status fem_batch_set_shape(fem_batch *batch, int nt_choice,
                                int blocks_per_sm, double timeout_ms);
 

@@ -116,6 +116,8 @@ def lib():
         "fem_precond_set_gamma": [_VP, ctypes.c_double],
         "fem_fcg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_batch_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
+        "fem_batch_create_split": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64,
+                                   ctypes.POINTER(_VP)],
         "fem_batch_destroy": [_VP],
         "fem_batch_solve": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                             ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
@@ -413,12 +415,25 @@ class Batch:
     solved together: FP64 refinement, the inner FP32 PCG of all problems in
     one persistent kernel per outer step (include/fem.h, fem_batch_*)."""
 
-    def __init__(self, ops):
+    SOLO_DOFS = 1 << 21   # FEM_BATCH_SOLO_DOFS
+
+    def __init__(self, ops, solo_dofs=None):
+        """solo_dofs: problems with at least this many unknowns are solved
+        one after another with their own refined solve instead of in the
+        persistent kernel (None: the library default, <= 0: never)."""
         self.ops = list(ops)
+        self.solo_dofs = self.SOLO_DOFS if solo_dofs is None else int(solo_dofs)
         arr = (_VP * len(self.ops))(*[o._h for o in self.ops])
         h = _VP()
-        _check(lib().fem_batch_create(arr, len(self.ops), ctypes.byref(h)))
+        _check(lib().fem_batch_create_split(arr, len(self.ops), self.solo_dofs, ctypes.byref(h)))
         self._h = h
+
+    @property
+    def solo(self):
+        """Indices of the problems solved alone."""
+        if self.solo_dofs <= 0:
+            return []
+        return [i for i, o in enumerate(self.ops) if o.n >= self.solo_dofs]
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -88,6 +88,12 @@ struct fem_batch {
   int bps = 0;                   // blocks per SM of the persistent kernel (0 = max)
   double timeout_ms = 2000.0;
   int64_t bytes = 0;
+  // Split batch: problems of at least solo_dofs unknowns are solved one
+  // after another by fem_solve_refined (order-specialized kernels); the rest
+  // form the persistent batch `inner`.  A split batch holds no device data.
+  bool split = false;
+  std::vector<int> solo, rest;
+  fem_batch *inner = nullptr;
 };
 
 namespace {
@@ -601,9 +607,8 @@ int run_solve(fem_batch *b, const fem_cg_opts *o, int *steps_out) {
 
 }  // namespace
 
-extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **out) {
-  if (!out || !ops || n < 1 || n > 1024) { fem_set_error("fem_batch_create: need 1..1024 operators"); return FEM_EINVAL; }
-  *out = nullptr;
+static int validate_ops(fem_op *const *ops, int n) {
+  if (!ops || n < 1 || n > 1024) { fem_set_error("fem_batch_create: need 1..1024 operators"); return FEM_EINVAL; }
   for (int i = 0; i < n; i++) {
     const fem_op *op = ops[i];
     if (!op || op->kind != FEM_DIFFUSION || op->quad != FEM_GAUSS || op->Q != op->P + 1 ||
@@ -617,6 +622,11 @@ extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **ou
       return FEM_EINVAL;
     }
   }
+  return FEM_OK;
+}
+
+// The persistent batch over all of ops (validated).
+static int create_persistent(fem_op *const *ops, int n, fem_batch **out) {
   fem_batch *b = new fem_batch();
   b->n = n;
   b->ops.assign(ops, ops + n);
@@ -718,8 +728,41 @@ extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **ou
   return FEM_OK;
 }
 
+extern "C" fem_status fem_batch_create_split(fem_op *const *ops, int n, int64_t solo_dofs,
+                                             fem_batch **out) {
+  if (!out) { fem_set_error("fem_batch_create: out is NULL"); return FEM_EINVAL; }
+  *out = nullptr;
+  int rc = validate_ops(ops, n);
+  if (rc) return rc;
+  std::vector<int> solo, rest;
+  for (int i = 0; i < n; i++) {
+    if (solo_dofs > 0 && ops[i]->N * ops[i]->ncomp >= solo_dofs) solo.push_back(i);
+    else rest.push_back(i);
+  }
+  if (solo.empty()) return create_persistent(ops, n, out);
+  fem_batch *b = new fem_batch();
+  b->n = n;
+  b->ops.assign(ops, ops + n);
+  b->stream = ops[0]->stream();
+  b->split = true;
+  b->solo = solo;
+  b->rest = rest;
+  if (!rest.empty()) {
+    std::vector<fem_op *> sub;
+    for (int i : rest) sub.push_back(ops[i]);
+    if ((rc = create_persistent(sub.data(), (int)sub.size(), &b->inner))) { delete b; return rc; }
+  }
+  *out = b;
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **out) {
+  return fem_batch_create_split(ops, n, FEM_BATCH_SOLO_DOFS, out);
+}
+
 extern "C" fem_status fem_batch_destroy(fem_batch *b) {
   if (!b) return FEM_OK;
+  if (b->inner) fem_batch_destroy(b->inner);
   for (void *p : b->allocs) cudaFree(p);
   delete b;
   return FEM_OK;
@@ -731,6 +774,7 @@ extern "C" fem_status fem_batch_set_shape(fem_batch *b, int nt_choice, int block
     fem_set_error("fem_batch_set_shape: invalid arguments");
     return FEM_EINVAL;
   }
+  if (b->split) return b->inner ? fem_batch_set_shape(b->inner, nt_choice, blocks_per_sm, timeout_ms) : FEM_OK;
   b->nt_choice = nt_choice;
   b->bps = blocks_per_sm;
   b->timeout_ms = timeout_ms;
@@ -751,6 +795,39 @@ static int bind_vectors(fem_batch *b, const double *const *bv, double *const *xv
   return FEM_OK;
 }
 
+// Split batch: the large problems one after another with their own
+// refined solves, then the persistent batch of the rest.
+static int solve_split(fem_batch *b, const double *const *bv, double *const *xv,
+                       const fem_cg_opts *o, fem_cg_stats *stats) {
+  for (int i = 0; i < b->n; i++) {
+    if (!bv[i] || !xv[i] || bv[i] == xv[i]) {
+      fem_set_error("fem_batch_solve: invalid vectors for problem %d", i);
+      return FEM_EINVAL;
+    }
+  }
+  int status = FEM_OK;
+  for (int i : b->solo) {
+    fem_cg_stats st = {};
+    const int rc = fem_solve_refined(b->ops[i], bv[i], xv[i], o, &st);
+    if (rc != FEM_OK && rc != FEM_ENOCONV && rc != FEM_EBREAKDOWN) return rc;
+    if (stats) stats[i] = st;
+    if (st.status != FEM_OK && status == FEM_OK) status = st.status;
+  }
+  if (b->inner) {
+    std::vector<const double *> sb;
+    std::vector<double *> sx;
+    std::vector<fem_cg_stats> ss(b->rest.size());
+    for (int i : b->rest) { sb.push_back(bv[i]); sx.push_back(xv[i]); }
+    const int rc = fem_batch_solve(b->inner, sb.data(), sx.data(), o, ss.data());
+    if (rc != FEM_OK && rc != FEM_ENOCONV && rc != FEM_EBREAKDOWN) return rc;
+    for (size_t k = 0; k < b->rest.size(); k++) {
+      if (stats) stats[b->rest[k]] = ss[k];
+      if (ss[k].status != FEM_OK && status == FEM_OK) status = ss[k].status;
+    }
+  }
+  return status;
+}
+
 static int reset_scalars(fem_batch *b) {
   std::vector<BatchScalars> z(b->n);
   memset(z.data(), 0, sizeof(BatchScalars) * b->n);
@@ -768,6 +845,7 @@ extern "C" fem_status fem_batch_solve(fem_batch *b, const double *const *bv, dou
     fem_set_error("fem_batch_solve: need Jacobi, rtol > 0, inner_rtol > 0, maxit >= 1, max_outer >= 1");
     return FEM_EINVAL;
   }
+  if (b->split) return solve_split(b, bv, xv, o, stats);
   int rc = bind_vectors(b, bv, xv);
   if (rc) return rc;
   if ((rc = reset_scalars(b))) return rc;
@@ -804,6 +882,11 @@ extern "C" fem_status fem_batch_solve(fem_batch *b, const double *const *bv, dou
 // timeout_ms; returns what the host reads (FEM_ETIMEOUT).  The batch stays
 // usable afterwards.
 extern "C" fem_status fem_batch_barrier_selftest(fem_batch *b, double timeout_ms) {
+  if (b && b->split) {
+    if (b->inner) return fem_batch_barrier_selftest(b->inner, timeout_ms);
+    fem_set_error("fem_batch_barrier_selftest: every problem of this batch is solved alone");
+    return FEM_EINVAL;
+  }
   if (!b || !(timeout_ms > 0) || b->h_prob[0].x == nullptr) {
     fem_set_error("fem_batch_barrier_selftest: invalid arguments (solve once first)");
     return FEM_EINVAL;
@@ -828,6 +911,16 @@ extern "C" fem_status fem_batch_barrier_selftest(fem_batch *b, double timeout_ms
 extern "C" fem_status fem_batch_autotune(fem_batch *b, const double *const *bv,
                                          double *const *xv, int iters, fem_tune_result *res) {
   if (!b || !bv || !xv || iters < 1) { fem_set_error("fem_batch_autotune: invalid arguments"); return FEM_EINVAL; }
+  if (b->split) {
+    if (!b->inner) {
+      if (res) { memset(res, 0, sizeof(*res)); res->epb_choice = b->nt_choice; }
+      return FEM_OK;
+    }
+    std::vector<const double *> sb;
+    std::vector<double *> sx;
+    for (int i : b->rest) { sb.push_back(bv[i]); sx.push_back(xv[i]); }
+    return fem_batch_autotune(b->inner, sb.data(), sx.data(), iters, res);
+  }
   int rc = bind_vectors(b, bv, xv);
   if (rc) return rc;
   const int bps_cand[] = {1, 2, 0};

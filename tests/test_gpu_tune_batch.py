@@ -151,3 +151,43 @@ def test_batch_barrier_runs_out_and_the_batch_stays_usable():
     xs = [torch.zeros_like(b) for b in bs]
     stats = batch.solve(bs, xs)
     assert all(s["status"] == "FEM_OK" and s["true_rel"] <= 1e-10 for s in stats)
+
+
+def test_split_batch_solves_large_problems_alone():
+    # problems with >= 3000 unknowns ((2, 8): 4913, (2, 7): 3375) go through
+    # the single-problem refined solve, the rest through the persistent kernel
+    probs = _batch_problems(SPECS)
+    batch = fem.Batch([p[2] for p in probs], solo_dofs=3000)
+    assert batch.solo == [3, 7]
+    xs = [torch.zeros_like(p[3]) for p in probs]
+    stats = batch.solve([p[3] for p in probs], xs, rtol=1e-10, inner_rtol=1e-5)
+    for (m, gm, op, b), x, st in zip(probs, xs, stats):
+        assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10, st
+        orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, m["p"] + 2)
+        bn = b.cpu().numpy()
+        res = np.where(m["dirichlet"] == 0, bn - orc.apply(x.cpu().numpy()), 0.0)
+        assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(bn)
+    # the shape and autotuner act on the persistent part
+    batch.set_shape(0, 1)
+    r = batch.autotune([p[3] for p in probs], [torch.zeros_like(p[3]) for p in probs], iters=3)
+    assert r["candidates"] == 9
+    assert batch.barrier_selftest(timeout_ms=200.0) == 6   # FEM_ETIMEOUT
+    xs = [torch.zeros_like(p[3]) for p in probs]
+    assert all(s["true_rel"] <= 1e-10 for s in batch.solve([p[3] for p in probs], xs))
+
+
+def test_batch_with_every_problem_alone():
+    probs = _batch_problems([(2, 3), (3, 2)])
+    batch = fem.Batch([p[2] for p in probs], solo_dofs=1)
+    assert batch.solo == [0, 1]
+    bs = [p[3] for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    stats = batch.solve(bs, xs)
+    for (m, gm, op, b), x, st in zip(probs, xs, stats):
+        x1 = torch.zeros_like(b)
+        st1 = op.solve_refined(b, x1, rtol=1e-10, inner_rtol=0.1)
+        assert st["true_rel"] <= 1e-10 and abs(st["iterations"] - st1["iterations"]) <= 6
+    batch.set_shape(1, 0)                        # nothing to shape: accepted
+    r = batch.autotune(bs, [torch.zeros_like(b) for b in bs], iters=2)
+    assert r["candidates"] == 0
+    assert batch.barrier_selftest(timeout_ms=100.0) == 1   # FEM_EINVAL: no persistent part
