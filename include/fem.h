@@ -473,6 +473,14 @@ fem_status fem_pmg_vcycle(fem_pmg *pmg, const double *r, double *z);
  * bnorm.  FEM_OK, FEM_ENOCONV or FEM_EBREAKDOWN. */
 fem_status fem_pmg_solve(fem_pmg *pmg, const double *b, double *x, const fem_cg_opts *opts,
                          fem_cg_stats *stats);
+/* The V-cycle as the preconditioner of fem_fcg_solve: B(r) = V(r), one FP32
+ * V-cycle (the hierarchy must have prec = FEM_F32 and a scalar finest level;
+ * it must outlive the preconditioner).  fem_fcg_solve then runs flexible CG
+ * in FP32 with FP64 iterative refinement around it: the FP64 operator is
+ * applied once per refinement step instead of once per iteration as in
+ * fem_pmg_solve.  fem_precond_apply gives z = V(r); set_gamma, features and
+ * samples do not apply. */
+fem_status fem_precond_create_pmg(fem_pmg *pmg, fem_precond **out);
 
 /* ------------------------------------------------------- allocation-free solve */
 

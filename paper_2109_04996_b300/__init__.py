@@ -109,6 +109,7 @@ def lib():
         "fem_mlp_train": [_VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                           ctypes.c_float, ctypes.c_uint64, _VP],
         "fem_precond_create": [_VP, _VP, ctypes.POINTER(_VP)],
+        "fem_precond_create_pmg": [_VP, ctypes.POINTER(_VP)],
         "fem_precond_destroy": [_VP],
         "fem_precond_features": [_VP, _VP],
         "fem_precond_samples": [_VP, _VP, _VP, _VP, _VP, _VP],
@@ -624,6 +625,9 @@ class Pmg:
         self._h = h
 
     def __del__(self):
+        if getattr(self, "_pc", None) and _lib is not None:
+            _lib.fem_precond_destroy(self._pc)
+            self._pc = None
         if getattr(self, "_h", None) and _lib is not None:
             _lib.fem_pmg_destroy(self._h)
             self._h = None
@@ -666,6 +670,35 @@ class Pmg:
         n = self.levels[0].n
         rc = lib().fem_pmg_solve(self._h, _vec(b, torch.float64, n, "b"), _vec(x, torch.float64, n, "x"),
                                  ctypes.byref(o), ctypes.byref(st))
+        if rc not in (0, 5):
+            _check(rc)
+        return _stats(st)
+
+    def _precond(self):
+        if getattr(self, "_pc", None) is None:
+            h = _VP()
+            _check(lib().fem_precond_create_pmg(self._h, ctypes.byref(h)))
+            self._pc = h
+        return self._pc
+
+    def vcycle_f32(self, r):
+        """z = V(r) through the FP32 preconditioner object (FP32 [n] in/out)."""
+        import torch
+        n = self.levels[0].n
+        z = torch.empty_like(r)
+        _check(lib().fem_precond_apply(self._precond(), _vec(r, torch.float32, n, "r"),
+                                       _vec(z, torch.float32, n, "z")))
+        return z
+
+    def solve_refined(self, b, x, rtol=1e-10, inner_rtol=1e-4, maxit=1000, max_outer=50):
+        """Flexible CG in FP32 around the FP32 V-cycle, inside FP64 iterative
+        refinement (fem_precond_create_pmg + fem_fcg_solve); needs prec=F32."""
+        import torch
+        n = self.levels[0].n
+        o = _CgOpts(PC_LEARNED, int(maxit), float(rtol), 1, float(inner_rtol), int(max_outer))
+        st = _CgStats()
+        rc = lib().fem_fcg_solve(self._precond(), _vec(b, torch.float64, n, "b"),
+                                 _vec(x, torch.float64, n, "x"), ctypes.byref(o), ctypes.byref(st))
         if rc not in (0, 5):
             _check(rc)
         return _stats(st)

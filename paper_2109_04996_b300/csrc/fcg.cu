@@ -4,7 +4,9 @@
 // Preconditioner  z = B(r) = dinv * r + sum_e G_e^T ( w * ||r_e|| f(r_e/||r_e||, g_e) )
 // with f the per-element MLP (mlp.cu), g_e element features (vertex offsets
 // from the centroid scaled by the element size, log kappa at the vertices),
-// w = 1 / node multiplicity.  B is nonlinear, so the Krylov method is
+// w = 1 / node multiplicity; or z = B(r) = V(r), one FP32 V-cycle of a
+// p-multigrid hierarchy (pmg.cu).  B is nonlinear (the network; the fixed-
+// count coarse PCG of the V-cycle), so the Krylov method is
 // flexible CG with one stored direction (Notay 2000):
 //   p_k = z_k - (z_k^T A p_{k-1} / p_{k-1}^T A p_{k-1}) p_{k-1},
 //   alpha_k = p_k^T r_k / p_k^T A p_k.
@@ -49,6 +51,7 @@ constexpr double kDrop = 0.25;
 struct fem_precond {
   fem_op *op = nullptr;
   fem_mlp *mlp = nullptr;      // null: Jacobi only
+  fem_pmg *pmg = nullptr;      // set: z = V(r), one FP32 p-multigrid V-cycle
   int64_t E = 0, N = 0, n = 0;
   int P3 = 0, n_in = 0, n_out = 0, esz = 2;
   float *feat = nullptr;       // [E][32]
@@ -346,8 +349,10 @@ __global__ void f_correct_kernel(const FParams c) {
   if (blockIdx.x == 0 && threadIdx.x == 0) c.sc->outer += 1;
 }
 
-// z (Jacobi part already in place) += learned correction of r
+// z (Jacobi part already in place) += learned correction of r; with a
+// p-multigrid hierarchy instead z = V(r)
 int launch_learned(fem_precond *pc, cudaStream_t s) {
+  if (pc->pmg) return fem_pmg_enqueue_vcycle32(pc->pmg, pc->r, pc->z, s);
   if (!pc->mlp) return FEM_OK;
   fem_op *op = pc->op;
   const int64_t warps_grid = 148 * 16;
@@ -404,10 +409,10 @@ int add_learned_if(fem_precond *pc, cudaStream_t s, cudaStream_t s2, cudaGraphCo
   fem_mesh *mesh = const_cast<fem_mesh *>(pc->op->mesh);
   cudaStream_t saved = mesh->stream, saved_mlp = nullptr;
   mesh->stream = s2;
-  fem_mlp_set_stream(pc->mlp, s2, &saved_mlp);
+  if (pc->mlp) fem_mlp_set_stream(pc->mlp, s2, &saved_mlp);
   if ((e = cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
     mesh->stream = saved;
-    fem_mlp_set_stream(pc->mlp, saved_mlp, nullptr);
+    if (pc->mlp) fem_mlp_set_stream(pc->mlp, saved_mlp, nullptr);
     *err = e;
     return FEM_ECUDA;
   }
@@ -415,7 +420,7 @@ int add_learned_if(fem_precond *pc, cudaStream_t s, cudaStream_t s2, cudaGraphCo
   cudaGraph_t tmp;
   cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
   mesh->stream = saved;
-  fem_mlp_set_stream(pc->mlp, saved_mlp, nullptr);
+  if (pc->mlp) fem_mlp_set_stream(pc->mlp, saved_mlp, nullptr);
   if (!rc && e2 != cudaSuccess) { *err = e2; rc = FEM_ECUDA; }
   return rc;
 }
@@ -450,17 +455,18 @@ int build_graph(fem_precond *pc, const double *b, double *x) {
     cudaGraphConditionalHandle h = 0, hl0 = 0, hl = 0;
     e = cudaStreamGetCaptureInfo(pc->cap, &st, nullptr, &graph, nullptr, nullptr, nullptr);
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess && pc->mlp)
+    const bool extra = pc->mlp || pc->pmg;   // preconditioner part behind an IF node
+    if (e == cudaSuccess && extra)
       e = cudaGraphConditionalHandleCreate(&hl0, graph, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
     FParams c = fparams(pc, b, x, h);
     c.learned = hl0;
-    c.has_learned = pc->mlp ? 1 : 0;
+    c.has_learned = extra ? 1 : 0;
     const int g = gridn(c.n);
     if ((rc = fem_launch_apply_f64(op, x, pc->y64, nullptr, op->E, nullptr))) break;
     f_residual_kernel<<<g, kT, 0, pc->cap>>>(c);
-    // IF (learned part active) { z += learned correction of r_0 }
-    if (pc->mlp) {
+    // IF (learned part active) { z += learned correction of r_0 } (or z = V(r_0))
+    if (extra) {
       if ((rc = add_learned_if(pc, pc->cap, pc->cap3, hl0, &e))) break;
     }
     f_restart_kernel<<<g, kT, 0, pc->cap>>>(c);  // p = p_old + (z - z_old), pr
@@ -480,14 +486,14 @@ int build_graph(fem_precond *pc, const double *b, double *x) {
     if (pc->mlp) fem_mlp_set_stream(pc->mlp, pc->cap2, nullptr);
     e = cudaStreamBeginCaptureToGraph(pc->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
-    if (pc->mlp && (e = cudaGraphConditionalHandleCreate(&hl, body, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+    if (extra && (e = cudaGraphConditionalHandleCreate(&hl, body, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
       rc = FEM_ECUDA;
     FParams cb = c;
     cb.learned = hl;
     if (!rc) rc = fem_launch_apply_f32(op, c.p, c.y, nullptr, op->E, &c.sc->pAp);
     if (!rc) {
       f_update_kernel<<<g, kT, 0, pc->cap2>>>(cb);
-      if (pc->mlp) rc = add_learned_if(pc, pc->cap2, pc->cap3, hl, &e);
+      if (extra) rc = add_learned_if(pc, pc->cap2, pc->cap3, hl, &e);
     }
     if (!rc) {
       f_dots_kernel<<<g, kT, 0, pc->cap2>>>(cb);
@@ -575,6 +581,21 @@ extern "C" fem_status fem_precond_create(fem_op *op, fem_mlp *mlp, fem_precond *
   return FEM_OK;
 }
 
+extern "C" fem_status fem_precond_create_pmg(fem_pmg *pmg, fem_precond **out) {
+  if (!pmg || !out) { fem_set_error("fem_precond_create_pmg: invalid arguments"); return FEM_EINVAL; }
+  *out = nullptr;
+  if (fem_pmg_precision(pmg) != FEM_F32) {
+    fem_set_error("fem_precond_create_pmg: the hierarchy must run its V-cycle in FEM_F32");
+    return FEM_EINVAL;
+  }
+  fem_precond *pc = nullptr;
+  int rc = fem_precond_create(fem_pmg_finest(pmg), nullptr, &pc);
+  if (rc) return rc;
+  pc->pmg = pmg;
+  *out = pc;
+  return FEM_OK;
+}
+
 extern "C" fem_status fem_precond_destroy(fem_precond *pc) {
   if (!pc) return FEM_OK;
   destroy_graph(pc);
@@ -647,7 +668,7 @@ extern "C" fem_status fem_fcg_solve(fem_precond *pc, const double *b, double *x,
   init.maxit = o->maxit;
   init.rtol2 = o->rtol * o->rtol;
   init.inner_rtol2 = o->inner_rtol * o->inner_rtol;
-  init.gamma = pc->mlp ? pc->gamma : 0.0;
+  init.gamma = pc->pmg ? 1.0 : (pc->mlp ? pc->gamma : 0.0);
   FEM_CUDA_TRY(cudaMemcpyAsync(pc->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   f_dinv_kernel<<<gridn(pc->n), kT, 0, s>>>(op->d_diag, op->mesh->d_dirichlet, pc->N, pc->n, pc->dinv);
   f_prepare_kernel<<<gridn(pc->n), kT, 0, s>>>(x, pc->y64, pc->p, pc->z, pc->y,

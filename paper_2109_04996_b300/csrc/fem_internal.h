@@ -144,6 +144,11 @@ inline int fem_apply_choices(const fem_op *op) {
   if (op->kind == FEM_DIFFUSION && !op->colloc && op->P == 2) return 7;
   return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
 }
+// ---- p-multigrid internals used by the refined flexible CG (pmg.cu)
+struct fem_pmg;
+int fem_pmg_enqueue_vcycle32(fem_pmg *m, const float *r, float *z, cudaStream_t s);
+fem_op *fem_pmg_finest(const fem_pmg *m);
+int fem_pmg_precision(const fem_pmg *m);
 // ---- setup (setup.cu)
 int fem_setup_qdata(fem_op *op);
 int fem_setup_diagonal(fem_op *op);

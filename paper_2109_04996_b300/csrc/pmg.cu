@@ -432,6 +432,11 @@ __global__ void to_f32_kernel(const double *a, float *b, int64_t n) {
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
+__global__ void copy_f32_kernel(const float *a, float *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
 __global__ void to_f64_kernel(const float *a, double *b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -547,6 +552,28 @@ struct StreamSwap {
       const_cast<fem_mesh *>(m->lv[i].op->mesh)->stream = saved[i];
   }
 };
+
+}  // namespace
+
+// One FP32 V-cycle z = V(r) between the caller's level-0 FP32 vectors,
+// enqueued on s (which may be capturing) with every level's mesh stream
+// pointed at s meanwhile.  Used by the refined flexible CG (fcg.cu); the
+// hierarchy must have prec = FEM_F32.
+int fem_pmg_enqueue_vcycle32(fem_pmg *m, const float *r, float *z, cudaStream_t s) {
+  Level &L = m->lv[0];
+  StreamSwap sw(m, s);
+  copy_f32_kernel<<<gridn(L.n), kT, 0, s>>>(r, L.v32.r, L.n);
+  FEM_CHECK_LAUNCH();
+  int rc = vcycle<float>(m, 0, s);
+  if (rc) return rc;
+  copy_f32_kernel<<<gridn(L.n), kT, 0, s>>>(L.v32.z, z, L.n);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+fem_op *fem_pmg_finest(const fem_pmg *m) { return m->lv[0].op; }
+int fem_pmg_precision(const fem_pmg *m) { return m->o.prec; }
+
+namespace {
 
 int build_vcycle_graph(fem_pmg *m) {
   if (m->vexec) return FEM_OK;

@@ -165,3 +165,40 @@ def test_pmg_zero_rhs_and_a_single_element():
     st = pm.solve(b, x, rtol=1e-10)
     assert st["status"] == "FEM_OK" and st["iterations"] == 0
     assert torch.count_nonzero(x).item() == 0
+
+
+def test_fp32_vcycle_as_preconditioner_of_refined_fcg():
+    meshes, gms, ops, pm, levels = _hierarchy(8, (4, 2, 1), prec=fem.F32, coarse_dq=1)
+    lmax = [opmg.power_lmax(L, 20) for L in levels[:-1]]
+    for l in range(2):
+        pm.set_lmax(l, lmax[l])
+    # B(r) of the preconditioner object is the V-cycle, against the oracle
+    rng = np.random.default_rng(8)
+    r = np.where(levels[0].inner, rng.uniform(-1, 1, levels[0].N), 0.0)
+    z = pm.vcycle_f32(torch.from_numpy(r).float().cuda()).double().cpu().numpy()
+    assert rel(z, opmg.vcycle(levels, lmax + [0.0], r, degree=4, coarse_its=30)) <= 1e-4
+    # refined FCG: FP64 true residual <= 1e-10 (oracle's apply), a couple of
+    # refinement steps, about the iterations of the FP64 flexible CG
+    m0 = meshes[0]
+    b = torch.from_numpy(fem_inputs.rhs_uniform(m0["N"], m0["dirichlet"], seed=9)).cuda()
+    x = torch.zeros_like(b)
+    st = pm.solve_refined(b, x, rtol=1e-10, inner_rtol=1e-4)
+    assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10, st
+    bn = np.where(levels[0].inner, b.cpu().numpy(), 0.0)
+    res = np.where(levels[0].inner, bn - levels[0].op.apply(x.cpu().numpy()), 0.0)
+    assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(bn)
+    assert 2 <= st["outer"] <= 4, st
+    x2 = torch.zeros_like(b)
+    st2 = pm.solve(b, x2, rtol=1e-10)
+    assert st["iterations"] <= st2["iterations"] + 4, (st, st2)
+    # a second solve replays the captured graph
+    x3 = torch.zeros_like(b)
+    st3 = pm.solve_refined(b, x3, rtol=1e-10, inner_rtol=1e-4)
+    assert st3["true_rel"] <= 1e-10 and abs(st3["iterations"] - st["iterations"]) <= 1
+
+
+def test_pmg_preconditioner_needs_fp32_hierarchy():
+    meshes, gms, ops, pm, levels = _hierarchy(3, (2, 1), prec=fem.F64)
+    with pytest.raises(fem.FemError):
+        pm.solve_refined(torch.zeros(levels[0].N, dtype=torch.float64, device="cuda"),
+                         torch.zeros(levels[0].N, dtype=torch.float64, device="cuda"))
