@@ -167,12 +167,12 @@ FP64_FMA_PER_SM_CLK = 2.0
 APPLY_F64_DRAM = {
     1: (3944312, 4019679, 5435637760, 65065984),
     2: (493039, 4019679, 1661260800, 46460416),
-    3: (148877, 4096000, 1019672832, 43075840),
+    3: (148877, 4096000, 1021982720, 43140352),
     4: (59319, 3869893, 713128704, 31546112),
     5: (32768, 4173281, 638709248, 32124160),
-    6: (17576, 3869893, 522269184, 30345728),
+    6: (17576, 3869893, 522320384, 29230080),
     7: (12167, 4251528, 524337408, 31831296),
-    8: (8000, 4173281, 476937216, 30977024),
+    8: (8000, 4173281, 474709504, 29166592),
 }
 
 

@@ -103,31 +103,44 @@ inline void make_symtab(const double *M, SymTab<T, NI, NO> &s) {
   }
 }
 
-// One cube of q^3 values in shared memory, x-contiguous.  For q a multiple
-// of 4 the innermost pitch is q+1: the threads of an x-line stage step
-// through shared memory by the pitch, and a pitch of 4 or 8 words would put
-// 4 or 8 of a warp's threads on one bank (measured: BP5/BP6 p=7 +3-15 %);
-// for q = 6 or 10 (2-way) the extra space costs more occupancy than it saves.
-// PAD = false keeps the pitch q (the batched kernel, which holds every order
-// in one kernel and is register-bound).
-template <int Q, bool PAD = true>
+// One cube of q^3 values in shared memory, x-contiguous: entry (k, j, i) at
+// i + sj j + sk k, cubes `size` words apart.  The stages read and write
+// whole lines along x, y and z with the warp's threads spread over the other
+// two directions (and over the elements of the group), so the strides decide
+// how many of a warp's accesses share a bank.  Plain layout: sj = q, sk =
+// q^2.  For q a multiple of 4 the pitch is q + 1 (a pitch of 4 or 8 words
+// puts 4 or 8 of an x-line stage's threads on one bank; BP5/BP6 p=7 +3-15 %).
+// FP32 at q = 4 and q = 10 uses the strides that minimize the words per bank
+// over every access instruction of both element bodies and the three
+// elements-per-block choices (counted on the host), measured faster at 8e6
+// DOFs: BP3 p=2 651 -> 515 us, BP5 p=3 185 -> 171 us, BP1 p=2 280 -> 242
+// us, BP3 p=8 226 -> 203 us.  (The same count favoured odd k-strides at q =
+// 5, 6, 7, 8, which measured 1-22 % slower: even strides let the compiler
+// pair the x-line accesses into 8-byte shared loads.)  PAD = false keeps
+// the plain layout (the batched kernel, which holds every order in one
+// kernel and is register-bound).
+template <int Q, bool PAD = true, int TSZ = 4>
 struct LineCube {
-  static constexpr int pitch = (PAD && Q % 4 == 0) ? Q + 1 : Q;
-  static constexpr int size = Q * Q * pitch;
+  static constexpr bool tuned = PAD && TSZ == 4 && (Q == 4 || Q == 10);
+  static constexpr bool pitch1 = PAD && !tuned && Q % 4 == 0;
+  static constexpr int sj = tuned ? Q : (pitch1 ? Q + 1 : Q);
+  static constexpr int sk = tuned ? (Q == 4 ? 19 : 105) : Q * sj;
+  static constexpr int size = tuned ? (Q == 4 ? 76 : 1049) : Q * Q * sj;
+  static_assert(size >= (Q - 1) * (1 + sj + sk) + 1, "cube entries must fit");
 };
 
 // Index of cube entry (k, j, i).  (A function, not a lambda: with a lambda
 // here the batched kernel, which inlines every order, took 119 registers
 // instead of 72.)
-template <int Q, int PITCH>
+template <int SJ, int SK>
 __device__ __forceinline__ int cube_ix(int k, int j, int i) {
-  return (k * Q + j) * PITCH + i;
+  return i + SJ * j + SK * k;
 }
 
 // Shared memory: 4 cubes per element slot.
 template <typename T, int Q, int EPB, bool PAD = true>
 constexpr size_t lines_smem_bytes() {
-  return sizeof(T) * (size_t)EPB * 4 * LineCube<Q, PAD>::size;
+  return sizeof(T) * (size_t)EPB * 4 * LineCube<Q, PAD, (int)sizeof(T)>::size;
 }
 
 // One thread's z-column of an element: its P node ids and gathered values.
@@ -175,7 +188,8 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   constexpr bool DIFF = KIND == FEM_DIFFUSION;
   static_assert(DIFF || !COLLOC, "the collocated mass operator is pointwise: slab body");
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P2 = P * P, P3 = P * P * P;
-  constexpr int CS = LineCube<Q, PAD>::size, PITCH = LineCube<Q, PAD>::pitch;
+  using Cube = LineCube<Q, PAD, (int)sizeof(T)>;
+  constexpr int CS = Cube::size, SJ = Cube::sj, SK = Cube::sk;
   const int slot_raw = threadIdx.x / Q2;
   const bool live = slot_raw < EPB;
   const int slot = live ? slot_raw : EPB - 1;
@@ -216,7 +230,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
     if constexpr (COLLOC) {
       if (on_pp) {
 #pragma unroll
-        for (int k = 0; k < Q; k++) c3[cube_ix<Q, PITCH>(k, lp1, lp0)] = u[k];
+        for (int k = 0; k < Q; k++) c3[cube_ix<SJ, SK>(k, lp1, lp0)] = u[k];
       }
     } else {
       // z-interpolation of the column (a, b)
@@ -224,27 +238,27 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T w[Q];
         sym_apply<+1>(tb.Bf, u, w);
 #pragma unroll
-        for (int k = 0; k < Q; k++) c1[cube_ix<Q, PITCH>(k, lp1, lp0)] = w[k];
+        for (int k = 0; k < Q; k++) c1[cube_ix<SJ, SK>(k, lp1, lp0)] = w[k];
       }
       __syncthreads();
       // y-lines (a, kq): c1[kq][0..P)[a] -> c2[kq][0..Q)[a]
       if (on_pq) {
         T in[P], out[Q];
 #pragma unroll
-        for (int j = 0; j < P; j++) in[j] = c1[cube_ix<Q, PITCH>(lp1, j, lp0)];
+        for (int j = 0; j < P; j++) in[j] = c1[cube_ix<SJ, SK>(lp1, j, lp0)];
         sym_apply<+1>(tb.Bf, in, out);
 #pragma unroll
-        for (int j = 0; j < Q; j++) c2[cube_ix<Q, PITCH>(lp1, j, lp0)] = out[j];
+        for (int j = 0; j < Q; j++) c2[cube_ix<SJ, SK>(lp1, j, lp0)] = out[j];
       }
       __syncthreads();
       // x-lines (jq, kq): c2[kq][jq][0..P) -> c3[kq][jq][0..Q)
       if (on_qq) {
         T in[P], out[Q];
 #pragma unroll
-        for (int i = 0; i < P; i++) in[i] = c2[cube_ix<Q, PITCH>(lq1, lq0, i)];
+        for (int i = 0; i < P; i++) in[i] = c2[cube_ix<SJ, SK>(lq1, lq0, i)];
         sym_apply<+1>(tb.Bf, in, out);
 #pragma unroll
-        for (int i = 0; i < Q; i++) c3[cube_ix<Q, PITCH>(lq1, lq0, i)] = out[i];
+        for (int i = 0; i < Q; i++) c3[cube_ix<SJ, SK>(lq1, lq0, i)] = out[i];
       }
     }
     __syncthreads();
@@ -254,7 +268,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       if (on_qq) {
 #pragma unroll
         for (int kq = 0; kq < Q; kq++) {
-          const int pt = cube_ix<Q, PITCH>(kq, lq1, lq0);
+          const int pt = cube_ix<SJ, SK>(kq, lq1, lq0);
           const T w = valid ? qd[(kq * Q + lq1) * Q + lq0] : T(0);
           c3[pt] *= w;
         }
@@ -266,22 +280,22 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       T in[Q], out[Q];
       // x-line (jq, kq) = (lq0, lq1)
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<Q, PITCH>(lq1, lq0, m)];
+      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<SJ, SK>(lq1, lq0, m)];
       sym_apply<-1>(tb.Df, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c1[cube_ix<Q, PITCH>(lq1, lq0, m)] = out[m];
+      for (int m = 0; m < Q; m++) c1[cube_ix<SJ, SK>(lq1, lq0, m)] = out[m];
       // y-line (iq, kq) = (lq0, lq1)
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<Q, PITCH>(lq1, m, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<SJ, SK>(lq1, m, lq0)];
       sym_apply<-1>(tb.Df, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c2[cube_ix<Q, PITCH>(lq1, m, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c2[cube_ix<SJ, SK>(lq1, m, lq0)] = out[m];
       // z-line (iq, jq) = (lq0, lq1)
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<Q, PITCH>(m, lq1, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<SJ, SK>(m, lq1, lq0)];
       sym_apply<-1>(tb.Df, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c4[cube_ix<Q, PITCH>(m, lq1, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c4[cube_ix<SJ, SK>(m, lq1, lq0)] = out[m];
     }
     __syncthreads();
     if constexpr (PIPE) column_values<T, P>(prm, *nxt);
@@ -289,11 +303,11 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
     if (on_qq) {
 #pragma unroll
       for (int kq = 0; kq < Q; kq++) {
-        const int pt = cube_ix<Q, PITCH>(kq, lq1, lq0);
+        const int pt = cube_ix<SJ, SK>(kq, lq1, lq0);
         T G00 = 0, G11 = 0, G22 = 0, G12 = 0, G02 = 0, G01 = 0;
         if (valid) {
           // qdata is unpadded: the cube index unless the cube is padded
-          const T *qk = qd + (LineCube<Q, PAD>::pitch == Q ? pt : (kq * Q + lq1) * Q + lq0);
+          const T *qk = qd + ((SJ == Q && SK == Q * Q) ? pt : (kq * Q + lq1) * Q + lq0);
           G00 = qk[0]; G11 = qk[Q3]; G22 = qk[2 * Q3];
           G12 = qk[3 * Q3]; G02 = qk[4 * Q3]; G01 = qk[5 * Q3];
         }
@@ -308,20 +322,20 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
     if (on_qq) {
       T in[Q], out[Q];
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c1[cube_ix<Q, PITCH>(lq1, lq0, m)];
+      for (int m = 0; m < Q; m++) in[m] = c1[cube_ix<SJ, SK>(lq1, lq0, m)];
       sym_apply<-1>(tb.Dt, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c1[cube_ix<Q, PITCH>(lq1, lq0, m)] = out[m];
+      for (int m = 0; m < Q; m++) c1[cube_ix<SJ, SK>(lq1, lq0, m)] = out[m];
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c2[cube_ix<Q, PITCH>(lq1, m, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c2[cube_ix<SJ, SK>(lq1, m, lq0)];
       sym_apply<-1>(tb.Dt, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c2[cube_ix<Q, PITCH>(lq1, m, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c2[cube_ix<SJ, SK>(lq1, m, lq0)] = out[m];
 #pragma unroll
-      for (int m = 0; m < Q; m++) in[m] = c4[cube_ix<Q, PITCH>(m, lq1, lq0)];
+      for (int m = 0; m < Q; m++) in[m] = c4[cube_ix<SJ, SK>(m, lq1, lq0)];
       sym_apply<-1>(tb.Dt, in, out);
 #pragma unroll
-      for (int m = 0; m < Q; m++) c4[cube_ix<Q, PITCH>(m, lq1, lq0)] = out[m];
+      for (int m = 0; m < Q; m++) c4[cube_ix<SJ, SK>(m, lq1, lq0)] = out[m];
     }
     __syncthreads();
     }  // DIFF
@@ -330,7 +344,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       if (on_pp) {
 #pragma unroll
         for (int k = 0; k < P; k++) {
-          const int pt = cube_ix<Q, PITCH>(k, lp1, lp0);
+          const int pt = cube_ix<SJ, SK>(k, lp1, lp0);
           const T s = c1[pt] + c2[pt] + c4[pt];
           if (valid) {
             const int64_t gi = PIPE ? cur->idx[k] : en[lp0 + P * lp1 + P2 * k];
@@ -348,29 +362,29 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T in[Q], out[P];
 #pragma unroll
         for (int m = 0; m < Q; m++) {
-          const int pt = cube_ix<Q, PITCH>(lq1, lq0, m);
+          const int pt = cube_ix<SJ, SK>(lq1, lq0, m);
           in[m] = DIFF ? c1[pt] + c2[pt] + c4[pt] : c3[pt];
         }
         sym_apply<+1>(tb.Bt, in, out);
 #pragma unroll
-        for (int i = 0; i < P; i++) c3[cube_ix<Q, PITCH>(lq1, lq0, i)] = out[i];
+        for (int i = 0; i < P; i++) c3[cube_ix<SJ, SK>(lq1, lq0, i)] = out[i];
       }
       __syncthreads();
       // y-lines (a, kq): c3[kq][0..Q)[a] -> c1[kq][0..P)[a]
       if (on_pq) {
         T in[Q], out[P];
 #pragma unroll
-        for (int j = 0; j < Q; j++) in[j] = c3[cube_ix<Q, PITCH>(lp1, j, lp0)];
+        for (int j = 0; j < Q; j++) in[j] = c3[cube_ix<SJ, SK>(lp1, j, lp0)];
         sym_apply<+1>(tb.Bt, in, out);
 #pragma unroll
-        for (int j = 0; j < P; j++) c1[cube_ix<Q, PITCH>(lp1, j, lp0)] = out[j];
+        for (int j = 0; j < P; j++) c1[cube_ix<SJ, SK>(lp1, j, lp0)] = out[j];
       }
       __syncthreads();
       // z-lines (a, b): c1[0..Q)[b][a] -> nodes, scatter
       if (on_pp) {
         T in[Q], out[P];
 #pragma unroll
-        for (int k = 0; k < Q; k++) in[k] = c1[cube_ix<Q, PITCH>(k, lp1, lp0)];
+        for (int k = 0; k < Q; k++) in[k] = c1[cube_ix<SJ, SK>(k, lp1, lp0)];
         sym_apply<+1>(tb.Bt, in, out);
 #pragma unroll
         for (int k = 0; k < P; k++) {

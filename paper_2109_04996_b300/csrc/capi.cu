@@ -212,30 +212,36 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   const int P = op->P, Q = op->Q;
   const int64_t Q3 = (int64_t)Q * Q * Q;
   const int nd = kind == FEM_DIFFUSION ? 6 : 1;
-  // default launch shapes (measured on B300, BP3 at 8e6 DOFs): FP32
-  // diffusion uses the line-based even-odd body; FP64 uses it from q = 5 on
-  // (Gauss; 1-6 % faster at p = 3..5), the slab body below (p = 1, 2: the
-  // even-odd saving is small and the slab's lower overhead wins, 8-11 %) and
-  // for the collocated operators
-  if (kind == FEM_DIFFUSION) {
-    // (p = 1 in FP32: the slab body with half the default elements per
-    // block, 3.4 vs 3.0 GDOF/s for the line body)
-    op->tune_epb[FEM_F32] = (!op->colloc && Q == 3) ? 4 : 0;
-    op->tune_epb[FEM_F64] = (!op->colloc && Q >= 5) ? 0 : 3;
-    if (!op->colloc && P == 2) {
-      // trilinear Gauss diffusion (8e6 DOFs): the thread-per-element body in
-      // FP64 (q = 3: 2.4x the slab body, q = 2: 1.3x) and in FP32 at q = 3
-      // with two blocks per SM (1.13x); FP32 at q = 2 keeps the slab body
-      op->tune_epb[FEM_F64] = 6;
-      if (Q == 3) { op->tune_epb[FEM_F32] = 6; op->tune_bps[FEM_F32] = 2; }
+  // Default launch shapes: the fastest choice (fem_apply_choices) of a
+  // sweep of every choice at 8e6 DOFs on a B300, per P = p + 1 (index P - 2):
+  // BP3 (Gauss q = p + 2), BP5 (collocated) and BP1 (Gauss mass).  Among
+  // them: the trilinear body (6) for Gauss diffusion at p = 1 (FP64 2.4x the
+  // slab body; FP32 at q = 3 with two blocks per SM), the slab body for FP64
+  // at p <= 2 and for most collocated FP64 orders, the line body elsewhere,
+  // often with half the default elements per block (1).
+  static const int kDiffF32[8] = {6, 1, 1, 0, 1, 0, 0, 1};
+  static const int kDiffF64[8] = {6, 3, 1, 0, 0, 1, 0, 2};
+  static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
+  static const int kCollF64[8] = {4, 3, 3, 4, 3, 3, 4, 2};
+  static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
+  static const int kMassF64[8] = {4, 4, 1, 0, 0, 1, 1, 1};
+  const int ip = P - 2;   // P in 2..9
+  if (kind == FEM_DIFFUSION && !op->colloc) {
+    op->tune_epb[FEM_F32] = kDiffF32[ip];
+    op->tune_epb[FEM_F64] = kDiffF64[ip];
+    if (P == 2) {
+      // trilinear: FP32 at q = 3 with two blocks per SM (2.09 vs 2.41 ms at
+      // the occupancy maximum); at q = 2 (the p-multigrid coarse level) the
+      // slab body with half the elements per block
+      if (Q == 3) op->tune_bps[FEM_F32] = 2;
       else op->tune_epb[FEM_F32] = 4;
     }
+  } else if (kind == FEM_DIFFUSION) {
+    op->tune_epb[FEM_F32] = kCollF32[ip];
+    op->tune_epb[FEM_F64] = kCollF64[ip];
   } else if (!op->colloc) {
-    // mass (BP1 at 8e6 DOFs): FP32 line body with half the default elements
-    // per block (2.4-3.2x the slab body for p >= 4); FP64 line body from
-    // q = 5 (half the elements per block from q = 9), slab body below
-    op->tune_epb[FEM_F32] = 1;
-    op->tune_epb[FEM_F64] = Q >= 9 ? 1 : (Q >= 5 ? 0 : 3);
+    op->tune_epb[FEM_F32] = kMassF32[ip];
+    op->tune_epb[FEM_F64] = kMassF64[ip];
   }
   int rc;
   double *tab = nullptr;
