@@ -306,9 +306,27 @@ template <int NT>
 __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
+  // problem i is inactive in iteration k once its done_at < k; done_at only
+  // changes in the direction phase (block 0), so the flags read at the top
+  // of an iteration hold for all its phases
+  __shared__ unsigned char s_inactive[1024];
+  __shared__ int s_active;
   const int64_t n_items = a.gstart[a.n], n_chunks = a.cstart[a.n];
   for (int k = 0; k < a.maxit; k++) {
     const int cur = k & 1, prev = cur ^ 1;
+    if (threadIdx.x == 0) s_active = 0;
+    __syncthreads();
+    {
+      int mine = 0;
+      for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        const bool off = __ldcg(&a.sc[i].done_at) < k;
+        s_inactive[i] = off ? 1 : 0;
+        mine += off ? 0 : 1;
+      }
+      if (mine) atomicAdd(&s_active, mine);
+    }
+    __syncthreads();
+    if (s_active == 0) return;   // every problem done (uniform across blocks)
     // -------- apply phase
     if (blockIdx.x == 0) {
       // rz[cur], rr[cur] were last read in the direction phase of k-1
@@ -323,7 +341,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
     double dot = 0.0;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
       const int i = find_problem(a.gstart, a.n, it);
-      if (__ldcg(&a.sc[i].done_at) < k) continue;   // uniform per block
+      if (s_inactive[i]) continue;   // uniform per block
       if (i != cur_prob) {
         if (cur_prob >= 0) {
           const double s = block_sum(dot, red);
@@ -343,7 +361,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
     // -------- update phase
     for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
       const int i = find_problem(a.cstart, a.n, it);
-      if (__ldcg(&a.sc[i].done_at) < k) continue;
+      if (s_inactive[i]) continue;
       const BatchProblem &pr = a.prob[i];
       const double pAp = __ldcg(&a.sc[i].pAp[cur]);
       const double alpha = __ldcg(&a.sc[i].rz[prev]) / pAp;
@@ -386,7 +404,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
     }
     for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
       const int i = find_problem(a.cstart, a.n, it);
-      if (__ldcg(&a.sc[i].done_at) < k) continue;
+      if (s_inactive[i]) continue;
       const BatchProblem &pr = a.prob[i];
       const float beta = (float)(__ldcg(&a.sc[i].rz[cur]) / __ldcg(&a.sc[i].rz[prev]));
       const int64_t lo = (it - a.cstart[i]) * kChunk;
@@ -397,9 +415,6 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
       }
     }
     if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
-    bool all = true;
-    for (int i = 0; i < a.n; i++) all = all && (__ldcg(&a.sc[i].done_at) <= k);
-    if (all) return;
   }
 }
 
@@ -893,13 +908,21 @@ extern "C" fem_status fem_batch_barrier_selftest(fem_batch *b, double timeout_ms
   }
   const double saved = b->timeout_ms;
   b->timeout_ms = timeout_ms;
-  int rc = reset_scalars(b);
-  if (rc) { b->timeout_ms = saved; return rc; }
+  // every problem active (done_at = INT_MAX), so that the kernel reaches
+  // its first grid barrier
+  std::vector<BatchScalars> h(b->n);
+  memset(h.data(), 0, sizeof(BatchScalars) * b->n);
+  for (auto &s : h) s.done_at = INT_MAX;
+  cudaError_t e = cudaMemcpyAsync(b->d_sc, h.data(), sizeof(BatchScalars) * b->n,
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    b->timeout_ms = saved;
+    fem_set_error("fem_batch_barrier_selftest: %s", cudaGetErrorString(e));
+    return FEM_ECUDA;
+  }
   BatchArgs a = args_of(b, 1, 1u);
-  // problems active (done_at = INT_MAX) so that the kernel reaches a barrier
-  batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a, 0.0, 0.0);
-  FEM_CHECK_LAUNCH();
-  rc = launch_inner(b, a, b->nt_choice, b->bps);
+  int rc = launch_inner(b, a, b->nt_choice, b->bps);
   b->timeout_ms = saved;
   if (rc) return rc;
   return read_error(b);
