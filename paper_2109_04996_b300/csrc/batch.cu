@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
       const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
       double v0 = 0.0, v1 = 0.0;
       for (int64_t j = lo + threadIdx.x; j < hi; j += NT) {
-        const bool fixed = pr.dir && pr.dir[j % pr.N];
+        const bool fixed = pr.dir && pr.dir[fem_node_of(j, pr.N)];
         float r = pr.r[j];
         pr.d[j] += af * pr.p[j];
         if (!fixed) r -= af * pr.y[j];  // atomics of other blocks, before the barrier
@@ -445,7 +445,7 @@ __global__ void batch_residual_kernel(const BatchArgs a) {
     const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
     double v[4] = {0, 0, 0, 0};
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-      const bool fixed = pr.dir && pr.dir[j % pr.N];
+      const bool fixed = pr.dir && pr.dir[fem_node_of(j, pr.N)];
       const double bj = fixed ? 0.0 : pr.b[j];
       const double r64 = fixed ? 0.0 : bj - pr.y64[j];
       const float r = (float)r64, z = pr.dinv[j] * r;
@@ -511,7 +511,7 @@ __global__ void batch_prepare_kernel(const BatchArgs a) {
     const int64_t lo = (it - a.cstart[i]) * kChunk;
     const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
     for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
-      const int64_t node = j % pr.N;
+      const int64_t node = fem_node_of(j, pr.N);
       if (pr.dir && pr.dir[node]) pr.x[j] = 0.0;
       pr.y64[j] = 0.0;
       pr.p[j] = 0.0f;

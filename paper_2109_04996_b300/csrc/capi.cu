@@ -382,7 +382,7 @@ namespace {
 __global__ void residual_kernel(const double *b, double *r, const uint8_t *dir, int64_t N, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    r[i] = (dir && dir[i % N]) ? 0.0 : b[i] - r[i];
+    r[i] = (dir && dir[fem_node_of(i, N)]) ? 0.0 : b[i] - r[i];
 }
 }  // namespace
 

@@ -48,7 +48,7 @@ __global__ void cg_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N
                                int pc, double *dinv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t node = i % N;
+    const int64_t node = fem_node_of(i, N);
     const bool fixed = dir && dir[node];
     dinv[i] = fixed ? 0.0 : (pc == FEM_PC_JACOBI ? 1.0 / diag[node] : 1.0);
   }
@@ -59,7 +59,7 @@ __global__ void cg_prepare_kernel(double *x, double *y, const uint8_t *dir, int6
                                   int64_t n, int zero) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (zero || (dir && dir[i % N])) x[i] = 0.0;
+    if (zero || (dir && dir[fem_node_of(i, N)])) x[i] = 0.0;
     y[i] = 0.0;
   }
 }
@@ -86,7 +86,7 @@ __global__ void cg_init_kernel(const CgParams c) {
   double v[3] = {0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const bool fixed = c.dir && c.dir[i % c.N];
+    const bool fixed = c.dir && c.dir[fem_node_of(i, c.N)];
     const double bi = fixed ? 0.0 : c.b[i];
     const double ri = fixed ? 0.0 : bi - c.y[i];
     const double zi = c.dinv[i] * ri;
@@ -121,7 +121,7 @@ __global__ void cg_update_kernel(const CgParams c) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
          i += (int64_t)gridDim.x * blockDim.x) {
       const double di = c.dinv[i];
-      const bool fixed = c.dir && c.dir[i % c.N];
+      const bool fixed = c.dir && c.dir[fem_node_of(i, c.N)];
       double ri = c.r[i];
       c.x[i] += alpha * c.p[i];
       if (!fixed) ri -= alpha * c.y[i];

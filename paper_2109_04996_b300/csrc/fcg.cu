@@ -213,7 +213,7 @@ __global__ void f_prepare_kernel(double *x, double *y64, float *p, float *z, flo
                                  const uint8_t *dir, int64_t N, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (dir && dir[i % N]) x[i] = 0.0;
+    if (dir && dir[fem_node_of(i, N)]) x[i] = 0.0;
     y64[i] = 0.0;
     p[i] = 0.0f; z[i] = 0.0f; y[i] = 0.0f;
   }
@@ -222,7 +222,7 @@ __global__ void f_prepare_kernel(double *x, double *y64, float *p, float *z, flo
 __global__ void f_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N, int64_t n, float *dinv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    dinv[i] = (dir && dir[i % N]) ? 0.0f : (float)(1.0 / diag[i % N]);
+    dinv[i] = (dir && dir[fem_node_of(i, N)]) ? 0.0f : (float)(1.0 / diag[fem_node_of(i, N)]);
 }
 
 // outer residual; inner start r = r64, d = 0, y = 0, z = dinv r (the learned
@@ -234,7 +234,7 @@ __global__ void f_residual_kernel(const FParams c) {
   double v[3] = {0, 0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const bool fixed = c.dir && c.dir[i % c.N];
+    const bool fixed = c.dir && c.dir[fem_node_of(i, c.N)];
     const double bi = fixed ? 0.0 : c.b[i];
     const double r64 = fixed ? 0.0 : bi - c.y64[i];
     const float r = (float)r64;
@@ -312,7 +312,7 @@ __global__ void f_update_kernel(const FParams c) {
   if (ok) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
          i += (int64_t)gridDim.x * blockDim.x) {
-      const bool fixed = c.dir && c.dir[i % c.N];
+      const bool fixed = c.dir && c.dir[fem_node_of(i, c.N)];
       float r = c.r[i];
       c.d[i] += af * c.p[i];
       if (!fixed) r -= af * c.y[i];

@@ -125,6 +125,13 @@ struct FemKernelCache {
 #define TAB_W (TAB_G + FEM_MAX_Q * FEM_MAX_P)
 #define TAB_SIZE (TAB_W + FEM_MAX_Q)
 
+// Node of entry i of a component-major vector of N-node components: i mod N
+// without the 64-bit division of `%` (tens of instructions per entry in the
+// bandwidth-bound vector kernels).  Operators have at most 3 components.
+__host__ __device__ __forceinline__ int64_t fem_node_of(int64_t i, int64_t N) {
+  return i < N ? i : (i < 2 * N ? i - N : (i < 3 * N ? i - 2 * N : i % N));
+}
+
 // ---- launchers (apply.cu)
 int fem_launch_apply_f64(fem_op *op, const double *x, double *y,
                          const int32_t *list, int64_t nsel, double *dot_out);

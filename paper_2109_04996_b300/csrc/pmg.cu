@@ -304,7 +304,7 @@ __global__ void cheb_step_kernel(T *t, T *y, T *d, T *z, const T *dinv, const T 
   const T a = (T)c1, b = (T)c2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const T tk = msk[i % N] * (t[i] - y[i]);
+    const T tk = msk[fem_node_of(i, N)] * (t[i] - y[i]);
     const T di = a * d[i] + b * dinv[i] * tk;
     t[i] = tk;
     d[i] = di;
@@ -318,7 +318,7 @@ template <typename T>
 __global__ void residual_kernel(const T *r, T *y, const T *msk, int64_t N, T *t, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    t[i] = msk[i % N] * (r[i] - y[i]);
+    t[i] = msk[fem_node_of(i, N)] * (r[i] - y[i]);
     y[i] = (T)0;
   }
 }
@@ -352,7 +352,7 @@ __global__ void cpcg_update_kernel(T *z, T *t, const T *d, const T *y, const T *
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     z[i] += a * d[i];
-    const T ti = msk[i % N] * (t[i] - a * y[i]);
+    const T ti = msk[fem_node_of(i, N)] * (t[i] - a * y[i]);
     t[i] = ti;
     v[0] += (double)ti * (double)(dinv[i] * ti);
   }
@@ -387,7 +387,7 @@ __global__ void power_start_kernel(const double *msk, int64_t N, int64_t n, doub
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double u = (double)(splitmix64_at(0ull, (unsigned long long)i) >> 11) * 0x1.0p-53 - 0.5;
-    v[i] = msk[i % N] * u;
+    v[i] = msk[fem_node_of(i, N)] * u;
     y[i] = 0.0;
   }
 }
@@ -624,7 +624,7 @@ __global__ void fcg_init_kernel(const FcgArgs a) {
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double m = a.msk[i % a.N];
+    const double m = a.msk[fem_node_of(i, a.N)];
     const double bi = m * a.b[i];
     const double ri = bi - m * a.y[i];
     a.r[i] = ri; a.p[i] = 0.0; a.y[i] = 0.0;
@@ -677,7 +677,7 @@ __global__ void fcg_update_kernel(const FcgArgs a) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
          i += (int64_t)gridDim.x * blockDim.x) {
       a.x[i] += alpha * a.p[i];
-      const double ri = a.msk[i % a.N] * (a.r[i] - alpha * a.y[i]);
+      const double ri = a.msk[fem_node_of(i, a.N)] * (a.r[i] - alpha * a.y[i]);
       a.r[i] = ri;
       v[0] += ri * ri;
     }

@@ -76,7 +76,7 @@ __global__ void rf_dinv_kernel(const double *diag, const uint8_t *dir, int64_t N
                                int pc, float *dinv) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t node = i % N;
+    const int64_t node = fem_node_of(i, N);
     dinv[i] = (dir && dir[node]) ? 0.0f : (pc == FEM_PC_JACOBI ? (float)(1.0 / diag[node]) : 1.0f);
   }
 }
@@ -86,7 +86,7 @@ __global__ void rf_prepare_kernel(double *x, double *y64, float *p, float *z, co
                                   int64_t N, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (dir && dir[i % N]) x[i] = 0.0;
+    if (dir && dir[fem_node_of(i, N)]) x[i] = 0.0;
     y64[i] = 0.0;
     p[i] = 0.0f;
     z[i] = 0.0f;
@@ -100,7 +100,7 @@ __global__ void rf_residual_kernel(const RParams c) {
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const bool fixed = c.dir && c.dir[i % c.N];
+    const bool fixed = c.dir && c.dir[fem_node_of(i, c.N)];
     const double bi = fixed ? 0.0 : c.b[i];
     const double r64 = fixed ? 0.0 : bi - c.y64[i];
     const float r = (float)r64;
@@ -138,7 +138,7 @@ __global__ void rf_update_kernel(const RParams c) {
   if (ok) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
          i += (int64_t)gridDim.x * blockDim.x) {
-      const bool fixed = c.dir && c.dir[i % c.N];
+      const bool fixed = c.dir && c.dir[fem_node_of(i, c.N)];
       float r = c.r[i];
       c.d[i] += af * c.p[i];
       if (!fixed) r -= af * c.y[i];
