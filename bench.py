@@ -889,9 +889,11 @@ def main():
             "gpu_launches": len(ops) * (2 + 3 * args.iters) * args.steps,
             "roofline": roofline, "clocks": clocks, "per_order": per_p}
     del ops
-    if args.tts_dofs > 0:
+    # the untimed single-GPU sections run at N = 1 only (a multi-rank run is
+    # the replicated headline sweep)
+    if args.tts_dofs > 0 and world == 1:
         line["time_to_solution"] = time_to_solution(fem, torch, args)
-    secs = [t for t in args.sections.split(",") if t]
+    secs = [t for t in args.sections.split(",") if t] if world == 1 else []
     if "bp56" in secs:
         line["bp5_bp6"] = section_bp56(fem, torch, args)
     if "suite" in secs:
