@@ -383,8 +383,12 @@ fem_status fem_batch_destroy(fem_batch *batch);
  * problems in lockstep outer steps; the inner iterations of all problems of
  * one outer step run in ONE persistent cooperative kernel (work items:
  * (problem, element group) and (problem, vector chunk); grid barriers with a
- * wall-clock limit).  Problems split off at creation are solved first, one
- * after another.  b, x: host arrays of n device pointers.  opts: precond
+ * wall-clock limit).  The outer loop runs as one CUDA graph (conditional
+ * WHILE node over the refinement steps, captured at the first solve and
+ * re-captured when the options or the launch shape change); where the runtime
+ * refuses to capture the cooperative launch, the steps are launched from the
+ * host instead (fem_batch_graph_state).  Problems split off at creation are
+ * solved first, one after another.  b, x: host arrays of n device pointers.  opts: precond
  * must be FEM_PC_JACOBI; rtol, inner_rtol, maxit (inner cap per step),
  * max_outer as in fem_solve_refined.  stats: host array of n (or NULL).
  * Returns the first non-OK problem status, or FEM_ETIMEOUT if a barrier ran
@@ -392,6 +396,10 @@ fem_status fem_batch_destroy(fem_batch *batch);
 fem_status fem_batch_solve(fem_batch *batch, const double *const *b,
                            double *const *x, const fem_cg_opts *opts,
                            fem_cg_stats *stats);
+/* How the persistent part's refinement loop runs: 1 = one captured CUDA graph,
+ * 0 = not captured yet (no solve so far, or nothing in the persistent
+ * kernel), -1 = capture refused by the runtime, host-launched steps. */
+fem_status fem_batch_graph_state(const fem_batch *batch, int *state);
 
 /* Launch shape of the persistent kernel: block size choice (0: 128, 1: 256,
  * 2: 512 threads), blocks per SM (0 = occupancy maximum) and the barrier

@@ -119,6 +119,7 @@ def lib():
         "fem_batch_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
         "fem_batch_create_split": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64,
                                    ctypes.POINTER(_VP)],
+        "fem_batch_graph_state": [_VP, ctypes.POINTER(ctypes.c_int)],
         "fem_batch_destroy": [_VP],
         "fem_batch_solve": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                             ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
@@ -467,6 +468,13 @@ class Batch:
         _check(lib().fem_batch_autotune(self._h, bv, xv, iters, ctypes.byref(r)))
         return dict(nt_choice=r.epb_choice, blocks_per_sm=r.blocks_per_sm, us_per_iter=r.us,
                     candidates=r.candidates)
+
+    def graph_state(self):
+        """1: the refinement loop runs as one CUDA graph; 0: not captured yet;
+        -1: capture refused, host-launched steps (fem_batch_graph_state)."""
+        v = ctypes.c_int()
+        _check(lib().fem_batch_graph_state(self._h, ctypes.byref(v)))
+        return v.value
 
     def barrier_selftest(self, timeout_ms=300.0):
         """Status code returned when the persistent kernel's barrier is made

@@ -94,6 +94,14 @@ struct fem_batch {
   bool split = false;
   std::vector<int> solo, rest;
   fem_batch *inner = nullptr;
+  // the refinement loop as one CUDA graph (conditional WHILE node over the
+  // outer steps), keyed by what its launches capture by value
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int *d_steps = nullptr;
+  int g_nt = -1, g_bps = -1, g_maxit = -1, g_max_outer = -1;
+  double g_rtol = -1.0, g_inner = -1.0, g_timeout = -1.0;
+  bool graph_refused = false;    // capture refused: host-driven outer loop
 };
 
 namespace {
@@ -586,26 +594,144 @@ int read_error(fem_batch *b) {
   return FEM_OK;
 }
 
-// Runs `steps` outer refinement steps (or until every problem converges).
-int run_solve(fem_batch *b, const fem_cg_opts *o, int *steps_out) {
+// Outer test of the graph-driven loop: stop once every problem converged,
+// after max_outer + 1 steps (as the host loop), or when a barrier ran out.
+__global__ void batch_decide_kernel(const BatchArgs a, int *steps, int max_outer,
+                                    cudaGraphConditionalHandle h) {
+  __shared__ int s_open;
+  if (threadIdx.x == 0) s_open = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+    if (!a.sc[i].converged) atomicOr(&s_open, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int st = *steps + 1;
+    *steps = st;
+    const bool stop = !s_open || st > max_outer || ((volatile BatchSync *)a.sync)->error;
+    cudaGraphSetConditional(h, stop ? 0u : 1u);
+  }
+}
+
+__global__ void batch_zero_steps_kernel(int *steps) { *steps = 0; }
+
+void destroy_solve_graph(fem_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+}
+
+// One outer refinement step (all problems) on stream s.
+int launch_outer_step(fem_batch *b, const BatchArgs &a, const fem_cg_opts *o, cudaStream_t s) {
   const int g = b->ops[0]->nsm * 8;
+  batch_apply64_kernel<<<b->ops[0]->nsm * 4, kNT64, batch_smem<double, kNT64>(), s>>>(a, b->d_gstart64);
+  FEM_CHECK_LAUNCH();
+  batch_residual_kernel<<<g, 256, 0, s>>>(a);
+  FEM_CHECK_LAUNCH();
+  batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(a, o->rtol * o->rtol,
+                                                          o->inner_rtol * o->inner_rtol);
+  FEM_CHECK_LAUNCH();
+  cudaStream_t saved = b->stream;
+  b->stream = s;   // the persistent kernel's launcher uses the batch stream
+  int rc = launch_inner(b, a, b->nt_choice, b->bps);
+  b->stream = saved;
+  if (rc) return rc;
+  batch_correct_kernel<<<g, 256, 0, s>>>(a);
+  FEM_CHECK_LAUNCH();
+  batch_step_end_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(a);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
+// Capture the refinement loop: steps = 0; WHILE (open) { outer step; decide }.
+// Returns FEM_ECUDA (error cleared) if the runtime refuses the capture, e.g.
+// of the cooperative launch inside the conditional body.
+int build_solve_graph(fem_batch *b, const fem_cg_opts *o) {
+  destroy_solve_graph(b);
+  if (!b->cap) {
+    FEM_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    FEM_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking));
+  }
+  BatchArgs a = args_of(b, o->maxit, 0);
+  cudaGraph_t graph = nullptr;
+  int rc = FEM_OK;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) { cudaGetLastError(); return FEM_ECUDA; }
+  do {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle h = 0;
+    e = cudaStreamGetCaptureInfo(b->cap, &st, nullptr, &graph, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
+    batch_zero_steps_kernel<<<1, 1, 0, b->cap>>>(b->d_steps);
+    e = cudaStreamGetCaptureInfo(b->cap, &st, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    if ((e = cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess) { rc = FEM_ECUDA; break; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamUpdateCaptureDependencies(b->cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
+    e = cudaStreamBeginCaptureToGraph(b->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { rc = FEM_ECUDA; break; }
+    rc = launch_outer_step(b, a, o, b->cap2);
+    if (!rc) {
+      batch_decide_kernel<<<1, 256, 0, b->cap2>>>(a, b->d_steps, o->max_outer, h);
+      if (cudaPeekAtLastError() != cudaSuccess) rc = FEM_ECUDA;
+    }
+    cudaGraph_t tmp;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap2, &tmp);
+    if (!rc && e2 != cudaSuccess) rc = FEM_ECUDA;
+  } while (0);
+  cudaGraph_t g2 = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(b->cap, &g2);
+  if (!rc && e3 != cudaSuccess) rc = FEM_ECUDA;
+  if (!rc && cudaGraphInstantiate(&b->gexec, g2, 0) != cudaSuccess) { b->gexec = nullptr; rc = FEM_ECUDA; }
+  if (g2) cudaGraphDestroy(g2);
+  if (rc) { cudaGetLastError(); return rc; }
+  b->g_nt = b->nt_choice; b->g_bps = b->bps; b->g_maxit = o->maxit; b->g_max_outer = o->max_outer;
+  b->g_rtol = o->rtol; b->g_inner = o->inner_rtol; b->g_timeout = b->timeout_ms;
+  return FEM_OK;
+}
+
+constexpr int kGraphRefused = -1;
+
+// The refinement loop as one graph launch; the host synchronizes once.
+int run_solve_graph(fem_batch *b, const fem_cg_opts *o, int *steps_out) {
+  const bool stale = !b->gexec || b->g_nt != b->nt_choice || b->g_bps != b->bps ||
+                     b->g_maxit != o->maxit || b->g_max_outer != o->max_outer ||
+                     b->g_rtol != o->rtol || b->g_inner != o->inner_rtol ||
+                     b->g_timeout != b->timeout_ms;
+  if (stale) {
+    FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));   // the capture streams must see prior work
+    if (build_solve_graph(b, o)) {
+      b->graph_refused = true;   // the host-driven loop from now on
+      return kGraphRefused;
+    }
+  }
+  FEM_CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
+  int rc = read_error(b);   // synchronizes
+  if (rc) return rc;
+  int steps = 0;
+  FEM_CUDA_TRY(cudaMemcpyAsync(&steps, b->d_steps, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  *steps_out = steps;
+  return FEM_OK;
+}
+
+// Runs outer refinement steps until every problem converges (or max_outer
+// + 1 steps), one host-launched step at a time.
+int run_solve(fem_batch *b, const fem_cg_opts *o, int *steps_out) {
   BatchArgs a = args_of(b, o->maxit, 0);
   std::vector<BatchScalars> h(b->n);
   int steps = 0;
   for (;;) {
-    batch_apply64_kernel<<<b->ops[0]->nsm * 4, kNT64, batch_smem<double, kNT64>(), b->stream>>>(a, b->d_gstart64);
-    FEM_CHECK_LAUNCH();
-    batch_residual_kernel<<<g, 256, 0, b->stream>>>(a);
-    FEM_CHECK_LAUNCH();
-    batch_finalize_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a, o->rtol * o->rtol,
-                                                                     o->inner_rtol * o->inner_rtol);
-    FEM_CHECK_LAUNCH();
-    int rc = launch_inner(b, a, b->nt_choice, b->bps);
+    int rc = launch_outer_step(b, a, o, b->stream);
     if (rc) return rc;
-    batch_correct_kernel<<<g, 256, 0, b->stream>>>(a);
-    FEM_CHECK_LAUNCH();
-    batch_step_end_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(a);
-    FEM_CHECK_LAUNCH();
     rc = read_error(b);
     if (rc) return rc;
     FEM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_sc, sizeof(BatchScalars) * b->n,
@@ -657,7 +783,8 @@ static int create_persistent(fem_op *const *ops, int n, fem_batch **out) {
             dalloc((void **)&b->d_sync, sizeof(BatchSync)) &&
             dalloc((void **)&b->d_gstart, sizeof(int64_t) * (n + 1)) &&
             dalloc((void **)&b->d_gstart64, sizeof(int64_t) * (n + 1)) &&
-            dalloc((void **)&b->d_cstart, sizeof(int64_t) * (n + 1));
+            dalloc((void **)&b->d_cstart, sizeof(int64_t) * (n + 1)) &&
+            dalloc((void **)&b->d_steps, sizeof(int));
   b->h_prob.resize(n);
   std::vector<int64_t> cs(n + 1, 0), g64(n + 1, 0);
   BatchLineTables htab;   // host image of the constant tables (uploaded per slot)
@@ -778,6 +905,9 @@ extern "C" fem_status fem_batch_create(fem_op *const *ops, int n, fem_batch **ou
 extern "C" fem_status fem_batch_destroy(fem_batch *b) {
   if (!b) return FEM_OK;
   if (b->inner) fem_batch_destroy(b->inner);
+  destroy_solve_graph(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap2) cudaStreamDestroy(b->cap2);
   for (void *p : b->allocs) cudaFree(p);
   delete b;
   return FEM_OK;
@@ -868,7 +998,8 @@ extern "C" fem_status fem_batch_solve(fem_batch *b, const double *const *bv, dou
   batch_prepare_kernel<<<b->ops[0]->nsm * 8, 256, 0, b->stream>>>(a);
   FEM_CHECK_LAUNCH();
   int steps = 0;
-  rc = run_solve(b, o, &steps);
+  rc = b->graph_refused ? kGraphRefused : run_solve_graph(b, o, &steps);
+  if (rc == kGraphRefused) rc = run_solve(b, o, &steps);
   if (rc) return rc;
   std::vector<BatchScalars> h(b->n);
   FEM_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_sc, sizeof(BatchScalars) * b->n,
@@ -890,6 +1021,17 @@ extern "C" fem_status fem_batch_solve(fem_batch *b, const double *const *bv, dou
     if (st != FEM_OK && status == FEM_OK) status = st;
   }
   return status;
+}
+
+extern "C" fem_status fem_batch_graph_state(const fem_batch *b, int *state) {
+  if (!b || !state) { fem_set_error("fem_batch_graph_state: invalid arguments"); return FEM_EINVAL; }
+  if (b->split) {
+    if (b->inner) return fem_batch_graph_state(b->inner, state);
+    *state = 0;
+    return FEM_OK;
+  }
+  *state = b->graph_refused ? -1 : (b->gexec ? 1 : 0);
+  return FEM_OK;
 }
 
 // Test hook of the bounded grid barrier: launches the persistent kernel with

@@ -97,8 +97,11 @@ SPECS = [(4, 2), (2, 5), (3, 3), (2, 8), (5, 1), (3, 4), (2, 6), (2, 7)]
 def test_batch_matches_single_solves_and_oracle():
     probs = _batch_problems(SPECS)
     batch = fem.Batch([p[2] for p in probs])
+    assert batch.graph_state() == 0
     xs = [torch.zeros_like(p[3]) for p in probs]
     stats = batch.solve([p[3] for p in probs], xs, rtol=1e-10, inner_rtol=1e-5)
+    # the refinement loop ran as one captured CUDA graph
+    assert batch.graph_state() == 1
     for (m, gm, op, b), x, st in zip(probs, xs, stats):
         assert st["status"] == "FEM_OK" and st["true_rel"] <= 1e-10, st
         orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, m["p"] + 2)
