@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--learned-n", type=int, default=64, help="elements per direction, kappa BP3 p=4")
     ap.add_argument("--profile", default=None,
                     help="only time the apply of one operator, e.g. BP5:7:f32 (problem:order:prec)"
-                         " on a mesh of --dofs nodes, or PMG:4:f32 for p-multigrid V-cycles;"
+                         " on a mesh of --dofs nodes, or PMG:4:f32 for p-multigrid V-cycles,"
+                         " BATCH:256:8 for the persistent batch kernel;"
                          " for profilers")
     return ap.parse_args()
 
@@ -672,6 +673,24 @@ def run_profile(args):
         flops = 2.0 * rows * (n_in * n_h + n_h * n_h + n_h * n_out)
         print(json.dumps({"profile": args.profile, "ms_per_forward": ms,
                           "tflops": flops / ms / 1e9}))
+        return
+    if args.profile.startswith("BATCH:"):
+        # the persistent batch kernel on the small-problem mix (count problems,
+        # n in 2..8, p in 1..4, seed): the autotuner launches it from the host,
+        # once per shape (block size 128, 256, 512 x blocks per SM 1, 2, max),
+        # each launch running --steps inner iterations of every problem
+        count, seed = (int(v) for v in args.profile.split(":")[1:])
+        specs = fem_inputs.batch_problems(count, seed=seed, nmin=2, nmax=8, pmin=1, pmax=4)
+        ops, bs = [], []
+        for s_ in specs:
+            m = fem_inputs.box_mesh(s_["n"], s_["p"], perturb=0.1, seed=s_["mesh_seed"])
+            ops.append(fem.Operator.bake_off(fem.Mesh(m), "BP3", prec=fem.F32))
+            bs.append(torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"],
+                                                              seed=s_["rhs_seed"])).cuda())
+        batch = fem.Batch(ops)
+        r = batch.autotune(bs, [torch.zeros_like(b) for b in bs], iters=args.steps)
+        print(json.dumps({"profile": args.profile, "problems": count,
+                          "dofs": sum(o.n for o in ops), "tune": r}))
         return
     name, p, prec = args.profile.split(":")
     p = int(p)
