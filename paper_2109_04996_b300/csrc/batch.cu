@@ -81,6 +81,12 @@ struct fem_batch {
   int64_t *d_gstart = nullptr;   // apply items prefix (inner shape)
   int64_t *d_gstart64 = nullptr; // apply items prefix (FP64 shape)
   int64_t *d_cstart = nullptr;   // vector chunk prefix
+  // problem of every work item: one load instead of a binary search over the
+  // prefixes at the head of each item's chain of dependent loads
+  int *d_item_prob = nullptr;    // apply items (inner shape), reallocated by build_items
+  int64_t item_prob_cap = 0;
+  int *d_item64_prob = nullptr;  // FP64 apply items
+  int *d_chunk_prob = nullptr;   // vector chunks
   int64_t n_items = 0, n_items64 = 0, n_chunks = 0;
   std::vector<BatchProblem> h_prob;
   std::vector<void *> allocs;
@@ -162,15 +168,6 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   if (threadIdx.x == 0)
     for (int w = 0; w < nw; w++) s += red[w];
   return s;  // valid in thread 0
-}
-
-__device__ __forceinline__ int find_problem(const int64_t *start, int n, int64_t item) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (start[mid] <= item) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 template <int NT, int Q>
@@ -303,6 +300,9 @@ struct BatchArgs {
   BatchSync *sync;
   const int64_t *gstart;   // [n+1] apply items
   const int64_t *cstart;   // [n+1] vector chunks
+  const int *item_prob;    // [n_items] problem of each apply item
+  const int *item64_prob;  // [n_items64] problem of each FP64 apply item
+  const int *chunk_prob;   // [n_chunks] problem of each vector chunk
   int n;
   int maxit;
   unsigned barrier_extra;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
     int cur_prob = -1;
     double dot = 0.0;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-      const int i = find_problem(a.gstart, a.n, it);
+      const int i = a.item_prob[it];
       if (s_inactive[i]) continue;   // uniform per block
       if (i != cur_prob) {
         if (cur_prob >= 0) {
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
     if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
     // -------- update phase
     for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
-      const int i = find_problem(a.cstart, a.n, it);
+      const int i = a.chunk_prob[it];
       if (s_inactive[i]) continue;
       const BatchProblem &pr = a.prob[i];
       const double pAp = __ldcg(&a.sc[i].pAp[cur]);
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
       }
     }
     for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
-      const int i = find_problem(a.cstart, a.n, it);
+      const int i = a.chunk_prob[it];
       if (s_inactive[i]) continue;
       const BatchProblem &pr = a.prob[i];
       const float beta = (float)(__ldcg(&a.sc[i].rz[cur]) / __ldcg(&a.sc[i].rz[prev]));
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(kNT64) batch_apply64_kernel(const BatchArgs a,
   const int64_t n_items = gstart64[a.n];
   int cur_prob = -1;
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int i = find_problem(gstart64, a.n, it);
+    const int i = a.item64_prob[it];
     if (a.sc[i].converged) continue;
     const BatchProblem &pr = a.prob[i];
     double dot = 0.0;
@@ -446,7 +446,7 @@ __global__ void batch_residual_kernel(const BatchArgs a) {
   __shared__ double red[32];
   const int64_t n_chunks = a.cstart[a.n];
   for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
-    const int i = find_problem(a.cstart, a.n, it);
+    const int i = a.chunk_prob[it];
     if (a.sc[i].converged) continue;
     const BatchProblem &pr = a.prob[i];
     const int64_t lo = (it - a.cstart[i]) * kChunk;
@@ -494,7 +494,7 @@ __global__ void batch_finalize_kernel(const BatchArgs a, double rtol2, double in
 __global__ void batch_correct_kernel(const BatchArgs a) {
   const int64_t n_chunks = a.cstart[a.n];
   for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
-    const int i = find_problem(a.cstart, a.n, it);
+    const int i = a.chunk_prob[it];
     if (a.sc[i].converged) continue;
     const BatchProblem &pr = a.prob[i];
     const int64_t lo = (it - a.cstart[i]) * kChunk;
@@ -514,7 +514,7 @@ __global__ void batch_step_end_kernel(const BatchArgs a) {
 __global__ void batch_prepare_kernel(const BatchArgs a) {
   const int64_t n_chunks = a.cstart[a.n];
   for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
-    const int i = find_problem(a.cstart, a.n, it);
+    const int i = a.chunk_prob[it];
     const BatchProblem &pr = a.prob[i];
     const int64_t lo = (it - a.cstart[i]) * kChunk;
     const int64_t hi = lo + kChunk < pr.n ? lo + kChunk : pr.n;
@@ -562,11 +562,33 @@ int64_t groups_for(const BatchProblem &p, int nt) {
   return (p.E + epb - 1) / epb;
 }
 
+// Problem of each of the n_items work items of a prefix table.
+std::vector<int> item_problems(const std::vector<int64_t> &start, int n) {
+  std::vector<int> m((size_t)start[n]);
+  for (int i = 0; i < n; i++)
+    for (int64_t it = start[i]; it < start[i + 1]; it++) m[(size_t)it] = i;
+  return m;
+}
+
 int build_items(fem_batch *b, int nt) {
   std::vector<int64_t> gs(b->n + 1, 0);
   for (int i = 0; i < b->n; i++) gs[i + 1] = gs[i] + groups_for(b->h_prob[i], nt);
   b->n_items = gs[b->n];
+  const std::vector<int> ip = item_problems(gs, b->n);
+  if (b->item_prob_cap < b->n_items) {
+    cudaFree(b->d_item_prob);
+    b->d_item_prob = nullptr;
+    b->item_prob_cap = 0;
+    if (cudaMalloc(&b->d_item_prob, sizeof(int) * (size_t)b->n_items) != cudaSuccess) {
+      cudaGetLastError();
+      fem_set_error("batch: allocation of the work-item table failed");
+      return FEM_ENOMEM;
+    }
+    b->item_prob_cap = b->n_items;
+  }
   FEM_CUDA_TRY(cudaMemcpyAsync(b->d_gstart, gs.data(), sizeof(int64_t) * (b->n + 1),
+                               cudaMemcpyHostToDevice, b->stream));
+  FEM_CUDA_TRY(cudaMemcpyAsync(b->d_item_prob, ip.data(), sizeof(int) * ip.size(),
                                cudaMemcpyHostToDevice, b->stream));
   FEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
   return FEM_OK;
@@ -576,6 +598,7 @@ BatchArgs args_of(fem_batch *b, int maxit, unsigned extra) {
   BatchArgs a;
   a.prob = b->d_prob; a.sc = b->d_sc; a.sync = b->d_sync; a.gstart = b->d_gstart;
   a.cstart = b->d_cstart; a.n = b->n; a.maxit = maxit; a.barrier_extra = extra;
+  a.item_prob = b->d_item_prob; a.item64_prob = b->d_item64_prob; a.chunk_prob = b->d_chunk_prob;
   a.timeout_ns = (unsigned long long)(b->timeout_ms * 1e6);
   return a;
 }
@@ -848,8 +871,17 @@ static int create_persistent(fem_op *const *ops, int n, fem_batch **out) {
   }
   b->n_chunks = cs[n];
   b->n_items64 = g64[n];
+  const std::vector<int> chunk_prob = item_problems(cs, n), item64_prob = item_problems(g64, n);
+  if (!dalloc((void **)&b->d_chunk_prob, sizeof(int) * chunk_prob.size()) ||
+      !dalloc((void **)&b->d_item64_prob, sizeof(int) * item64_prob.size())) {
+    fem_set_error("fem_batch_create: device allocation failed");
+    fem_batch_destroy(b);
+    return FEM_ENOMEM;
+  }
   cudaError_t e = cudaMemcpyAsync(b->d_cstart, cs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_gstart64, g64.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_chunk_prob, chunk_prob.data(), sizeof(int) * chunk_prob.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_item64_prob, item64_prob.data(), sizeof(int) * item64_prob.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
@@ -908,6 +940,7 @@ extern "C" fem_status fem_batch_destroy(fem_batch *b) {
   destroy_solve_graph(b);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->cap2) cudaStreamDestroy(b->cap2);
+  cudaFree(b->d_item_prob);
   for (void *p : b->allocs) cudaFree(p);
   delete b;
   return FEM_OK;
