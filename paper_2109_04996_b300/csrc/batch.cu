@@ -170,6 +170,21 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return s;  // valid in thread 0
 }
 
+// Two block sums with one pair of barriers (red holds 64 doubles).
+__device__ __forceinline__ void block_sum2(double &v0, double &v1, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v0 = fem_warp_sum(v0);
+  v1 = fem_warp_sum(v1);
+  __syncthreads();
+  if (lane == 0) { red[warp] = v0; red[32 + warp] = v1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < nw; w++) { s0 += red[w]; s1 += red[32 + w]; }
+    v0 = s0; v1 = s1;   // valid in thread 0
+  }
+}
+
 template <int NT, int Q>
 struct BatchEpb {
   static constexpr int value = NT / (Q * Q) > 0 ? NT / (Q * Q) : 1;
@@ -313,7 +328,7 @@ struct BatchArgs {
 template <int NT>
 __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32];
+  __shared__ double red[64];
   // problem i is inactive in iteration k once its done_at < k; done_at only
   // changes in the direction phase (block 0), so the flags read at the top
   // of an iteration hold for all its phases
@@ -389,11 +404,10 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         v0 += (double)r * (double)z;
         v1 += (double)r * (double)r;
       }
-      const double s0 = block_sum(v0, red);
-      const double s1 = block_sum(v1, red);
+      block_sum2(v0, v1, red);
       if (threadIdx.x == 0) {
-        atomicAdd(&a.sc[i].rz[cur], s0);
-        atomicAdd(&a.sc[i].rr[cur], s1);
+        atomicAdd(&a.sc[i].rz[cur], v0);
+        atomicAdd(&a.sc[i].rr[cur], v1);
       }
     }
     if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
