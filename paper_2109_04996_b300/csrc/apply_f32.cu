@@ -3,7 +3,8 @@
 #include "apply_dispatch.cuh"
 
 int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32_t *list,
-                               int64_t nsel, double *dot_out, int choice, int bps) {
+                               int64_t nsel, double *dot_out, int choice, int bps,
+                               const int *skip) {
   if (!op->d_qdata32) {
     fem_set_error("apply_f32: operator was not created with FEM_F32");
     return FEM_EINVAL;
@@ -15,12 +16,13 @@ int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32
   prm.N = op->N; prm.ncomp = op->ncomp;
   prm.qdata = op->d_qdata32; prm.B = op->d_B32; prm.Dq = op->d_Dq32;
   prm.partials = op->d_partials; prm.counter = op->d_counter; prm.dot_out = dot_out;
+  prm.skip = skip;
   if (nsel == 0) return FEM_OK;
   return fem_apply::dispatch<float>(op, prm, choice, bps);
 }
 
 int fem_launch_apply_f32(fem_op *op, const float *x, float *y, const int32_t *list,
-                         int64_t nsel, double *dot_out) {
+                         int64_t nsel, double *dot_out, const int *skip) {
   return fem_launch_apply_f32_shape(op, x, y, list, nsel, dot_out, op->tune_epb[FEM_F32],
-                                    op->tune_bps[FEM_F32]);
+                                    op->tune_bps[FEM_F32], skip);
 }

@@ -43,7 +43,16 @@ struct ApplyParams {
                               // other blocks of a persistent kernel)
   int want_dot = 0;           // 1: accumulate x.y into the caller's `dot` even
                               // without dot_out (persistent batch kernel)
+  const int *skip = nullptr;  // *skip != 0: the launch does nothing (a solve
+                              // whose loop body outlived its convergence)
 };
+
+// Uniform early exit of a launch whose solve has finished (read once, before
+// any barrier, by every thread).
+template <typename T>
+__device__ __forceinline__ bool apply_skipped(const ApplyParams<T> &prm) {
+  return prm.skip && *(volatile const int *)prm.skip;
+}
 
 // Accumulator of a thread's share of x.y over one element.  FP64: plain.
 // FP32: compensated (double-float) on the FP32 pipe -- each product is split
@@ -451,6 +460,7 @@ template <typename T, int P, int Q, int KIND, bool COLLOC, int EPB>
 __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     fem_apply_kernel(const ApplyParams<T> prm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (apply_skipped(prm)) return;
   Slab<T, P, Q, KIND, EPB> sl(smem_raw);
   sl.load_tables(prm.B, prm.Dq);
   __syncthreads();

@@ -412,6 +412,7 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *cubes = reinterpret_cast<T *>(smem_raw);
   const ApplyParams<T> &prm = lp.a;
+  if (apply_skipped(prm)) return;
   double dot = 0.0;
   const int64_t ngroups = (prm.nsel + EPB - 1) / EPB;
   if constexpr (PIPE) {

@@ -51,6 +51,7 @@ template <typename T, int Q>
 __global__ void __launch_bounds__(kTrilinearThreads)
     fem_apply_trilinear_kernel(const TrilinearParams<T, Q> tp) {
   const ApplyParams<T> &prm = tp.a;
+  if (apply_skipped(prm)) return;
   const TrilinearTables<T, Q> &t = tp.t;
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
   DotAcc<T> dl;

@@ -36,6 +36,7 @@ struct CgWork {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kUnroll = 4;   // CG iterations per pass of the graph's WHILE body
 
 int grid_for(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
@@ -152,7 +153,7 @@ __global__ void cg_update_kernel(const CgParams c) {
 
 __global__ void cg_direction_kernel(const CgParams c) {
   const double beta = c.sc->beta;
-  if (c.sc->done && !c.use_graph) return;
+  if (c.sc->done) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     c.p[i] = c.z[i] + beta * c.p[i];
@@ -208,7 +209,8 @@ int launch_prologue(fem_op *op, const CgParams &c, cudaStream_t s, int zero_gues
 
 int launch_body(fem_op *op, const CgParams &c, cudaStream_t s) {
   const int g = grid_for(c.n);
-  int rc = fem_launch_apply_f64(op, c.p, c.y, nullptr, op->E, &c.sc->pAp);
+  // the apply does nothing once the solve is done (unrolled graph bodies)
+  int rc = fem_launch_apply_f64(op, c.p, c.y, nullptr, op->E, &c.sc->pAp, &c.sc->done);
   if (rc) return rc;
   cg_update_kernel<<<g, kThreads, 0, s>>>(c);
   FEM_CHECK_LAUNCH();
@@ -270,7 +272,10 @@ static int build_graph(fem_op *op, const double *b, double *x, int zero_guess) {
     mesh->stream = w->cap2;
     e = cudaStreamBeginCaptureToGraph(w->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) { rc = FEM_ECUDA; goto end_capture; }
-    rc = launch_body(op, c, w->cap2);
+    // kUnroll iterations per pass of the WHILE body: the conditional node's
+    // per-pass cost is paid once per kUnroll iterations; iterations after
+    // convergence within a pass do nothing (their kernels test `done`)
+    for (int u = 0; u < kUnroll && !rc; u++) rc = launch_body(op, c, w->cap2);
     {
       cudaGraph_t tmp;
       cudaError_t e2 = cudaStreamEndCapture(w->cap2, &tmp);

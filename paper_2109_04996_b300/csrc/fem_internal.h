@@ -133,16 +133,22 @@ __host__ __device__ __forceinline__ int64_t fem_node_of(int64_t i, int64_t N) {
 }
 
 // ---- launchers (apply.cu)
+// skip: optional device flag; nonzero when the launch runs makes it a no-op
+// (the loop body of a solve that has converged)
 int fem_launch_apply_f64(fem_op *op, const double *x, double *y,
-                         const int32_t *list, int64_t nsel, double *dot_out);
+                         const int32_t *list, int64_t nsel, double *dot_out,
+                         const int *skip = nullptr);
 int fem_launch_apply_f32(fem_op *op, const float *x, float *y,
-                         const int32_t *list, int64_t nsel, double *dot_out);
+                         const int32_t *list, int64_t nsel, double *dot_out,
+                         const int *skip = nullptr);
 // explicit launch shape (autotuner): body / elements-per-block choice
 // (fem_apply_choices), blocks per SM (0 = max)
 int fem_launch_apply_f64_shape(fem_op *op, const double *x, double *y, const int32_t *list,
-                               int64_t nsel, double *dot_out, int choice, int bps);
+                               int64_t nsel, double *dot_out, int choice, int bps,
+                               const int *skip = nullptr);
 int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32_t *list,
-                               int64_t nsel, double *dot_out, int choice, int bps);
+                               int64_t nsel, double *dot_out, int choice, int bps,
+                               const int *skip = nullptr);
 // Launch shape choices of an operator's apply: 0..2 the line-based body
 // (elements per block default, half, double), 3..5 the slab body, 6 the
 // trilinear body (Gauss diffusion at p = 1); the collocated mass operator
