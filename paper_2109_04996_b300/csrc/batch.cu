@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "apply_lines.cuh"
+#include "grid_sync.cuh"
 
 using fem_apply::ApplyParams;
 using fem_apply::LineTables;
@@ -65,11 +66,7 @@ struct BatchScalars {
   int total_iter, outer, converged, status;
 };
 
-struct BatchSync {
-  unsigned count, gen;
-  int error;
-  int pad;
-};
+using BatchSync = FemGridSync;
 
 struct fem_batch {
   int n = 0;
@@ -114,49 +111,6 @@ namespace {
 
 constexpr int kChunk = 2048;     // vector entries per work item
 constexpr int kNT64 = 256;       // block size of the FP64 batched apply
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid barrier with a wall-clock limit.  Returns false (every block) once
-// any block has recorded an error.  Memory written before the barrier by any
-// block is visible to ordinary loads after it: thread 0 fences (fence.sc at
-// GPU scope) before arriving and after seeing the release, and the block's
-// bar.sync orders its other threads after thread 0.  extra: arrivals that never come (a test
-// hook that makes the wait run out); 0 in normal use.
-__device__ bool grid_barrier(BatchSync *s, unsigned extra, unsigned long long timeout_ns) {
-  __syncthreads();
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    volatile unsigned *vgen = &s->gen;
-    volatile int *verr = &s->error;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&s->count, 1u);
-    if (arrived == gridDim.x + extra - 1) {
-      atomicExch(&s->count, 0u);
-      __threadfence();
-      atomicAdd(&s->gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (*vgen == g) {
-        if (*verr) break;
-        if (global_ns() - t0 > timeout_ns) {
-          atomicCAS(&s->error, 0, (int)FEM_ETIMEOUT);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __threadfence();
-    s_ok = (*verr == 0);
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -271,7 +225,7 @@ __device__ void batch_group_lines(const BatchProblem &pr, int64_t g, unsigned ch
   prm.N = pr.N; prm.ncomp = pr.ncomp;
   prm.qdata = pr.qdata32; prm.B = pr.B32; prm.Dq = pr.Dq32;
   prm.partials = nullptr; prm.counter = nullptr; prm.dot_out = nullptr;
-  prm.x_l2_only = 0;  // written before the last grid barrier (see grid_barrier)
+  prm.x_l2_only = 0;  // written before the last grid barrier (see fem_grid_barrier)
   prm.want_dot = 1;   // p^T A p of the problem
   apply_group_lines<float, P, Q, false, EPB, false, false>(prm, batch_ltab<P>(), g, cubes, dot);
 }
@@ -380,7 +334,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
       const double s = block_sum(dot, red);
       if (threadIdx.x == 0) atomicAdd(&a.sc[cur_prob].pAp[cur], s);
     }
-    if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
+    if (!fem_grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
     // -------- update phase
     for (int64_t it = blockIdx.x; it < n_chunks; it += gridDim.x) {
       const int i = a.chunk_prob[it];
@@ -410,7 +364,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         atomicAdd(&a.sc[i].rr[cur], v1);
       }
     }
-    if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
+    if (!fem_grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
     // -------- direction phase
     if (blockIdx.x == 0) for (int ii = threadIdx.x; ii < a.n; ii += blockDim.x) {
       BatchScalars &s = a.sc[ii];
@@ -436,7 +390,7 @@ __global__ void __launch_bounds__(NT) batch_inner_kernel(const BatchArgs a) {
         pr.y[j] = 0.0f;
       }
     }
-    if (!grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
+    if (!fem_grid_barrier(a.sync, a.barrier_extra, a.timeout_ns)) return;
   }
 }
 

@@ -114,6 +114,24 @@ def test_single_level_is_the_coarse_pcg():
     assert rel(z, opmg.coarse_pcg(L, r, 7)) <= 1e-11
 
 
+@pytest.mark.parametrize("q", [2, 3])
+@pytest.mark.parametrize("its", [1, 2, 9, 30])
+def test_coarse_pcg_on_a_trilinear_level_matches_oracle(q, its):
+    # the usual coarsest level (p = 1, Gauss q = 2 or 3); 11^3 elements span
+    # several blocks
+    m = fem_inputs.box_mesh(11, 1, perturb=0.1, seed=7, shuffle_seed=3)
+    L = opmg.Level(m, q=q)
+    r = np.where(L.inner, np.random.default_rng(its).uniform(-1, 1, L.N), 0.0)
+    ref = opmg.coarse_pcg(L, r, its)
+    for prec, tol in ((fem.F64, 1e-11), (fem.F32, 1e-4)):
+        op = fem.Operator(fem.Mesh(m), fem.DIFFUSION, fem.GAUSS, q, prec=prec)
+        pm = fem.Pmg([op], coarse_its=its, prec=prec)
+        z = pm.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+        assert rel(z, ref) <= tol, (prec, rel(z, ref))
+        z2 = pm.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()   # graph replay
+        assert rel(z2, ref) <= tol
+
+
 @pytest.mark.parametrize("prec", [fem.F64, fem.F32])
 def test_pmg_fcg_solves_to_1e10_in_few_iterations(prec):
     meshes, gms, ops, pm, levels = _hierarchy(8, (4, 2, 1), prec=prec)
