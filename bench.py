@@ -905,7 +905,9 @@ def main():
             "data": "synthetic", "config": config(args, work),
             "e2e": {"value": dof_it * world / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
-            "gpu_launches": len(ops) * (2 + 3 * args.iters) * args.steps,
+            # per order: prepare + init, then 3 kernels per iteration in
+            # passes of 4 (kernels after the last iteration return at once)
+            "gpu_launches": len(ops) * (2 + 3 * 4 * ((args.iters + 3) // 4)) * args.steps,
             "roofline": roofline, "clocks": clocks, "per_order": per_p}
     del ops
     # the untimed single-GPU sections run at N = 1 only (a multi-rank run is
