@@ -90,12 +90,13 @@ def executed_flops(p, n):
     """FP64 flops the default body executes per BP3 apply (FMA = 2).  Equal to
     the algorithmic count except at p = 1, where the trilinear body uses that
     each gradient component is constant along its own direction: per element
-    18q^3 (D) + 21q^2 + 42q (face differences, interpolations and their
-    transposes) + 44 (vertex sums, x.y)."""
+    12q^3 (off-diagonal D) + 6q^2 (diagonal D through its line sums) + 21q^2
+    + 42q (face differences, interpolations and their transposes) + 44
+    (vertex sums, x.y)."""
     N, E, _, flops = algorithmic(p, n)
     if p == 1:
         q = 3
-        return E * (18 * q ** 3 + 21 * q * q + 42 * q + 44)
+        return E * (12 * q ** 3 + 27 * q * q + 42 * q + 44)
     return flops
 
 
@@ -162,11 +163,13 @@ FP64_FMA_PER_SM_CLK = 2.0
 # DRAM bytes of one FP64 BP3 apply per order, from one ncu capture
 # (dram__bytes_read.sum, dram__bytes_write.sum) of `bench.py --profile
 # BP3:<p>:f64 --dofs 4e6` on a B300: (E, N, read, write) of the captured mesh.
-# The ratio to the algorithmic bytes (1.03-1.07) is steady across sizes (the
-# bytes are qdata, indices and the two vectors, all proportional to the mesh),
-# so the full-size traffic is that ratio times the full-size algorithmic bytes.
+# The ratio to the algorithmic bytes (1.03-1.07; 0.79 at p = 1, whose body
+# reads the off-diagonal qdata and the line sums of the diagonal) is steady
+# across sizes (the bytes are qdata, indices and the two vectors, all
+# proportional to the mesh), so the full-size traffic is that ratio times the
+# full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 5435637760, 65065984),
+    1: (3944312, 4019679, 4138469120, 63885824),
     2: (493039, 4019679, 1661260800, 46460416),
     3: (148877, 4096000, 1021982720, 43140352),
     4: (59319, 3869893, 713128704, 31546112),
@@ -892,7 +895,7 @@ def main():
                 "executed_tflops": tot_exec / tot_time / 1e12,
                 "executed_frac": tot_exec / tot_time / 1e12 / fp64_peak,
                 "executed_note": "achieved counts the formula's flops per element; the p = 1"
-                                 " trilinear body executes 44 % of them (executed_flops)",
+                                 " trilinear body executes 39 % of them (executed_flops)",
                 "kernel": "FP64 fused apply (trilinear body p=1, slab body p=2, line body p>=3),"
                           " all orders",
                 "hbm_achieved_gbs": tot_bytes / tot_time / 1e9, "hbm_peak_gbs": hbm_peak,

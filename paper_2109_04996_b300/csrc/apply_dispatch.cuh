@@ -103,6 +103,12 @@ template <typename T, int Q>
 int launch_trilinear(fem_op *op, const ApplyParams<T> &prm, int bps) {
   TrilinearParams<T, Q> tp;
   tp.a = prm;
+  if constexpr (sizeof(T) == 8) tp.qsum = reinterpret_cast<const T *>(op->d_qsum);
+  else tp.qsum = reinterpret_cast<const T *>(op->d_qsum32);
+  if (!tp.qsum) {
+    fem_set_error("apply: the trilinear body needs the operator's qdata line sums");
+    return FEM_EINVAL;
+  }
   for (int k = 0; k < Q; k++)
     for (int a = 0; a < 2; a++) {
       tp.t.B[k][a] = (T)op->tab.B[k * 2 + a];

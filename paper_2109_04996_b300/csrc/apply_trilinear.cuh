@@ -21,13 +21,18 @@
 //   Sx[j][k] = sum_i vx(i, j, k),  Sy[i][k] = sum_j vy,  Sz[i][j] = sum_k vz,
 //
 // and y[a][b][c] += (2a-1) rx[b][c] + (2b-1) ry[a][c] + (2c-1) rz[a][b] with
-// rx[b][c] = sum_j B[j][b] sum_k H[k][c] Sx[j][k] (likewise ry, rz).
+// rx[b][c] = sum_j B[j][b] sum_k H[k][c] Sx[j][k] (likewise ry, rz).  In Sx
+// the term D00 gx has gx constant along i, so it is gx[j][k] times the line
+// sum of D00 over i, computed once at set-up (fem_op::d_qsum; likewise D11
+// in Sy, D22 in Sz): per point only the three off-diagonal entries are read
+// and applied.
 //
-// At q = 3 this takes about 460 FP64 operations per element against about
-// 1050 lane-slots of the slab body: the B300's FP64 pipe (2 FMA per SM per
-// clock) is the bound of the FP64 apply, so the instruction count is what
-// matters.  Everything stays in registers; qdata is read in quadrature-point
-// order, so a thread's consecutive loads of one component share sectors.
+// At q = 3 this takes about 400 FP64 operations per element (737 flops)
+// against about 1050 lane-slots of the slab body: the B300's FP64 pipe
+// (2 FMA per SM per clock) is the bound of the FP64 apply, so the
+// instruction count is what matters.  Everything stays in registers; qdata is
+// read in quadrature-point order, so a thread's consecutive loads of one
+// component share sectors.
 #pragma once
 #include "apply_kernel.cuh"
 
@@ -43,6 +48,7 @@ template <typename T, int Q>
 struct TrilinearParams {
   ApplyParams<T> a;
   TrilinearTables<T, Q> t;
+  const T *qsum;   // [E][3][Q^2] line sums of D00, D11, D22 (fem_op::d_qsum)
 };
 
 constexpr int kTrilinearThreads = 128;
@@ -50,8 +56,8 @@ constexpr int kTrilinearThreads = 128;
 // Element e: y += A_e x_e (all components) and this thread's share of x.y.
 template <typename T, int Q>
 __device__ __forceinline__ void trilinear_element(const ApplyParams<T> &prm,
-                                                  const TrilinearTables<T, Q> &t, int64_t e,
-                                                  DotAcc<T> &dl) {
+                                                  const TrilinearTables<T, Q> &t,
+                                                  const T *qsum, int64_t e, DotAcc<T> &dl) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
   int id[8];
   {
@@ -111,14 +117,26 @@ __device__ __forceinline__ void trilinear_element(const ApplyParams<T> &prm,
 #pragma unroll
         for (int i = 0; i < Q; i++) {
           const T *qk = qd + i + Q * j + Q2 * k;
-          const T G00 = qk[0], G11 = qk[Q3], G22 = qk[2 * Q3];
           const T G12 = qk[3 * Q3], G02 = qk[4 * Q3], G01 = qk[5 * Q3];
           const T ax = gx[j][k], ay = gy[i][k], az = gz[i][j];
-          // one multiply-add per term (9 per point)
-          Sx[j][k] += G00 * ax; Sx[j][k] += G01 * ay; Sx[j][k] += G02 * az;
-          Sy[i][k] += G01 * ax; Sy[i][k] += G11 * ay; Sy[i][k] += G12 * az;
-          Sz[i][j] += G02 * ax; Sz[i][j] += G12 * ay; Sz[i][j] += G22 * az;
+          // the off-diagonal terms, one multiply-add each (6 per point); a
+          // diagonal term's gradient is constant along the line it is summed
+          // over, so it enters below through the line sum of its D entry
+          Sx[j][k] += G01 * ay; Sx[j][k] += G02 * az;
+          Sy[i][k] += G01 * ax; Sy[i][k] += G12 * az;
+          Sz[i][j] += G02 * ax; Sz[i][j] += G12 * ay;
         }
+    {
+      const T *qs = qsum + e * (int64_t)(3 * Q2);
+#pragma unroll
+      for (int l = 0; l < Q; l++)
+#pragma unroll
+        for (int m = 0; m < Q; m++) {
+          Sx[l][m] += qs[l + Q * m] * gx[l][m];            // sum_i D00(i, l, m)
+          Sy[l][m] += qs[Q2 + l + Q * m] * gy[l][m];       // sum_j D11(l, j, m)
+          Sz[l][m] += qs[2 * Q2 + l + Q * m] * gz[l][m];   // sum_k D22(l, m, k)
+        }
+    }
     // transposed interpolations: r[s][r] per direction
     T rx[2][2], ry[2][2], rz[2][2];
     {
@@ -173,7 +191,7 @@ __global__ void __launch_bounds__(kTrilinearThreads)
   DotAcc<T> dl;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k_el = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k_el < prm.nsel; k_el += stride)
-    trilinear_element<T, Q>(prm, tp.t, prm.list ? (int64_t)prm.list[k_el] : k_el, dl);
+    trilinear_element<T, Q>(prm, tp.t, tp.qsum, prm.list ? (int64_t)prm.list[k_el] : k_el, dl);
   if (prm.dot_out) {
     double v[1] = {dl.get()};
     __shared__ double tot[1];

@@ -21,6 +21,26 @@ int dev_alloc(T **p, size_t count, int64_t *bytes) {
   return FEM_OK;
 }
 
+// Line sums of the diagonal qdata components of trilinear elements (see
+// fem_op::d_qsum): one thread per (element, component, line), summed in FP64.
+__global__ void qdata_line_sums_kernel(const double *qd, int64_t E, int Q, double *qsum) {
+  const int Q2 = Q * Q, Q3 = Q2 * Q;
+  const int64_t total = E * 3 * Q2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / (3 * Q2);
+    const int r = (int)(t - e * 3 * Q2), c = r / Q2, l = r - c * Q2;
+    const int u = l % Q, v = l / Q;   // the two coordinates the line does not run along
+    const double *q = qd + e * 6 * Q3 + (int64_t)c * Q3;
+    double s = 0.0;
+    for (int m = 0; m < Q; m++) {
+      const int pt = c == 0 ? m + Q * u + Q2 * v : (c == 1 ? u + Q * m + Q2 * v : u + Q * v + Q2 * m);
+      s += q[pt];
+    }
+    qsum[t] = s;
+  }
+}
+
 __global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -229,12 +249,10 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   if (kind == FEM_DIFFUSION && !op->colloc) {
     op->tune_epb[FEM_F32] = kDiffF32[ip];
     op->tune_epb[FEM_F64] = kDiffF64[ip];
-    if (P == 2) {
-      // trilinear: FP32 at q = 3 with two blocks per SM (2.09 vs 2.41 ms at
-      // the occupancy maximum); at q = 2 (the p-multigrid coarse level) the
-      // slab body with half the elements per block
-      if (Q == 3) op->tune_bps[FEM_F32] = 2;
-      else op->tune_epb[FEM_F32] = 4;
+    if (P == 2 && Q == 3) {
+      // trilinear FP32 at q = 3 with two blocks per SM (1.28 vs 1.29 ms at
+      // the occupancy maximum, 8e6 DOFs)
+      op->tune_bps[FEM_F32] = 2;
     }
   } else if (kind == FEM_DIFFUSION) {
     op->tune_epb[FEM_F32] = kCollF32[ip];
@@ -286,6 +304,16 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
     if ((rc = dev_alloc(&op->d_qdata32, nq, &op->bytes))) { fem_op_destroy(op); return rc; }
     if (nq > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qdata, op->d_qdata32, (int64_t)nq);
   }
+  if (kind == FEM_DIFFUSION && !op->colloc && P == 2) {
+    // the trilinear body applies the diagonal of D once per line
+    const size_t ns = (size_t)op->E * 3 * Q * Q;
+    if ((rc = dev_alloc(&op->d_qsum, ns, &op->bytes))) { fem_op_destroy(op); return rc; }
+    if (ns > 0) qdata_line_sums_kernel<<<148 * 8, 256, 0, s>>>(op->d_qdata, op->E, Q, op->d_qsum);
+    if (prec == FEM_F32) {
+      if ((rc = dev_alloc(&op->d_qsum32, ns, &op->bytes))) { fem_op_destroy(op); return rc; }
+      if (ns > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qsum, op->d_qsum32, (int64_t)ns);
+    }
+  }
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -304,6 +332,7 @@ extern "C" fem_status fem_op_destroy(fem_op *op) {
   if (op->d_B) cudaFree(op->d_B - TAB_B);
   if (op->d_B32) cudaFree(op->d_B32 - TAB_B);
   cudaFree(op->d_qdata); cudaFree(op->d_qdata32); cudaFree(op->d_diag); cudaFree(op->d_rff);
+  cudaFree(op->d_qsum); cudaFree(op->d_qsum32);
   cudaFree(op->d_partials); cudaFree(op->d_counter);
   delete op;
   return FEM_OK;

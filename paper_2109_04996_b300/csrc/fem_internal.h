@@ -85,6 +85,11 @@ struct fem_op {
   float *d_B32 = nullptr, *d_Dq32 = nullptr;
   double *d_qdata = nullptr;      // [E][nd][Q^3]
   float *d_qdata32 = nullptr;     // FP32 copy (prec == FEM_F32)
+  // trilinear Gauss diffusion only (P = 2): line sums of the diagonal qdata
+  // components, [E][3][Q^2]: sum over i of D00 at (j, k) (index j + Q k),
+  // over j of D11 at (i, k) (i + Q k), over k of D22 at (i, j) (i + Q j)
+  double *d_qsum = nullptr;
+  float *d_qsum32 = nullptr;
   double *d_diag = nullptr;       // [N] scalar diagonal
   double *d_rff = nullptr;        // [M][4]
   int M = 0;
