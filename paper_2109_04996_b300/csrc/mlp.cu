@@ -181,8 +181,8 @@ int gemm(const fem_mlp *n, const GemmArgs &a, bool AT, bool BT) {
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, fem_mlp_tc::kSmemBytes));
       set = 1;
     }
-    dim3 grid((unsigned)((a.M + fem_mlp_tc::TM - 1) / fem_mlp_tc::TM),
-              (unsigned)((a.N + fem_mlp_tc::TN - 1) / fem_mlp_tc::TN), (unsigned)ks);
+    if (tiles > 0x7fffffff) { fem_set_error("mlp gemm: %lld output tiles", (long long)tiles); return FEM_EINVAL; }
+    dim3 grid((unsigned)tiles, 1, (unsigned)ks);
     fem_mlp_tc::gemm_tc_kernel<<<grid, fem_mlp_tc::NT, fem_mlp_tc::kSmemBytes, s>>>(t);
     FEM_CHECK_LAUNCH();
     return FEM_OK;

@@ -23,10 +23,10 @@
 
 namespace fem_mlp_tc {
 
-constexpr int TM = 128, TN = 128, TK = 32, NT = 128, NS = 4;
+constexpr int TM = 128, TN = 128, TK = 32, NT = 128, NS = 3;
 constexpr int kTileBytes = TM * TK * 2;           // 8 KB per operand and stage
 constexpr int kStageBytes = 2 * kTileBytes;       // A and B
-constexpr int kSmemBytes = NS * kStageBytes + 1024;   // 65 KB: 3 CTAs / SM (TMEM: 3 x 128 columns)
+constexpr int kSmemBytes = NS * kStageBytes + 1024;   // 49 KB: 4 CTAs / SM (TMEM: 4 x 128 columns)
 constexpr unsigned long long kWaitLimit = 1ull << 22;   // try_wait polls before giving up
 
 struct TcArgs {
@@ -89,6 +89,13 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
   else asm volatile("cp.async.wait_group 3;\n" ::: "memory");
 }
 
+// Two FP32 values as packed bf16 (round to nearest even), lo at the lower
+// address.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
 // Copies of K stage `st` (columns [k0 + st*TK, k0 + st*TK + TK), below
 // kend) into stage buffer b.
 __device__ __forceinline__ void load_stage(const TcArgs &g, unsigned char *buf, int st, int64_t row0,
@@ -118,8 +125,12 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = (int64_t)blockIdx.x * TM;
-  const int col0 = blockIdx.y * TN;
+  // blockIdx.x runs over the output tiles with the column tiles of a row
+  // block adjacent: they read the same rows of A, which the later ones find
+  // in L2
+  const int ntn = (g.N + TN - 1) / TN;
+  const int64_t row0 = (int64_t)(blockIdx.x / ntn) * TM;
+  const int col0 = (int)(blockIdx.x % ntn) * TN;
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int b = 0; b < NS; b++)
@@ -196,10 +207,14 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (!s_fail && nst > 0) {
-    // ---- epilogue.  The stage buffers are free now: the bias of the tile's
-    // columns and one 32-column chunk of the accumulator at a time are
-    // staged there, so that each warp can store its 32 rows with the lanes
-    // along the columns (coalesced) instead of one row per lane.
+    // ---- epilogue.  After tcgen05.ld a lane holds 32 consecutive columns
+    // of its own row.  Plain stores (vec): the lane writes them as 16-byte
+    // vectors (bf16: 4, fp32: 8), one 64- or 128-byte row segment.  Atomic
+    // adds (split K) or unaligned C: each 32-column chunk is staged in the
+    // free stage buffers so that a warp adds its 32 rows with the lanes
+    // along the columns.  The tile's bias is staged there in both cases.
+    const bool vec = !g.accumulate && g.ldc % 8 == 0 && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 &&
+                     (!g.mask || (g.ldm % 8 == 0 && (reinterpret_cast<uintptr_t>(g.mask) & 15) == 0));
     float *stile = reinterpret_cast<float *>(smem);        // [128][33]
     float *sbias = stile + TM * 33;                          // [TN]
     for (int i = threadIdx.x; i < TN; i += NT)
@@ -220,6 +235,59 @@ __global__ void __launch_bounds__(NT) gemm_tc_kernel(const TcArgs g) {
             "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (vec) {
+        const int64_t row = row0 + rloc;
+        const int cbase = col0 + cb;
+        if (row < g.M) {
+          float x[32];
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            x[j] = __uint_as_float(v[j]) + sbias[cb + j];
+            if (g.relu) x[j] = x[j] > 0.0f ? x[j] : 0.0f;
+          }
+          if (cbase + 32 <= g.N) {
+            if (g.mask) {
+              const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + row * g.ldm + cbase);
+#pragma unroll
+              for (int q = 0; q < 4; q++) {
+                const uint4 m = mp[q];
+                const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                  if (!(__uint_as_float(w[t] << 16) > 0.0f)) x[8 * q + 2 * t] = 0.0f;
+                  if (!(__uint_as_float(w[t] & 0xffff0000u) > 0.0f)) x[8 * q + 2 * t + 1] = 0.0f;
+                }
+              }
+            }
+            if (g.out_bf16) {
+              uint4 *cp = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(g.C) + row * g.ldc + cbase);
+#pragma unroll
+              for (int q = 0; q < 4; q++)
+                cp[q] = make_uint4(pack_bf16x2(x[8 * q], x[8 * q + 1]), pack_bf16x2(x[8 * q + 2], x[8 * q + 3]),
+                                   pack_bf16x2(x[8 * q + 4], x[8 * q + 5]), pack_bf16x2(x[8 * q + 6], x[8 * q + 7]));
+            } else {
+              float4 *cp = reinterpret_cast<float4 *>(reinterpret_cast<float *>(g.C) + row * g.ldc + cbase);
+#pragma unroll
+              for (int q = 0; q < 8; q++) cp[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            }
+          } else {
+            // the ragged last chunk of N
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+              const int col = cbase + j;
+              if (col < g.N) {
+                float y = x[j];
+                if (g.mask && !(__bfloat162float(g.mask[row * g.ldm + col]) > 0.0f)) y = 0.0f;
+                if (g.out_bf16)
+                  reinterpret_cast<__nv_bfloat16 *>(g.C)[row * g.ldc + col] = __float2bfloat16(y);
+                else
+                  reinterpret_cast<float *>(g.C)[row * g.ldc + col] = y;
+              }
+            }
+          }
+        }
+        continue;
+      }
 #pragma unroll
       for (int j = 0; j < 32; j++) stile[rloc * 33 + j] = __uint_as_float(v[j]);
       __syncwarp();
