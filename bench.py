@@ -86,18 +86,27 @@ def algorithmic(p, n):
     return N, E, bytes_, flops
 
 
+ELMAT_ORDERS = (1, 2)   # FP64 default body: assembled element matrices
+
+
+def body_algorithmic(p, n):
+    """Per FP64 BP3 apply with the default body: bytes that must move and
+    flops it executes (FMA = 2).  p >= 3, sum factorization: algorithmic().
+    p = 1, 2, element matrices: 16N (x, y) + 4 E P^3 (indices) + 8 E P^3
+    (P^3 + 1) / 2 (the packed upper triangle of K_e), and 2 (P^3)^2 flops
+    per element for y_e = K_e x_e (each off-diagonal entry used twice) plus
+    2 P^3 for x.y."""
+    N, E, by, fl = algorithmic(p, n)
+    if p in ELMAT_ORDERS:
+        P3 = (p + 1) ** 3
+        by = 16 * N + 4 * E * P3 + 8 * E * P3 * (P3 + 1) // 2
+        fl = E * (2 * P3 * P3 + 2 * P3)
+    return N, E, by, fl
+
+
 def executed_flops(p, n):
-    """FP64 flops the default body executes per BP3 apply (FMA = 2).  Equal to
-    the algorithmic count except at p = 1, where the trilinear body uses that
-    each gradient component is constant along its own direction: per element
-    12q^3 (off-diagonal D) + 6q^2 (diagonal D through its line sums) + 21q^2
-    + 42q (face differences, interpolations and their transposes) + 44
-    (vertex sums, x.y)."""
-    N, E, _, flops = algorithmic(p, n)
-    if p == 1:
-        q = 3
-        return E * (12 * q ** 3 + 27 * q * q + 42 * q + 44)
-    return flops
+    """FP64 flops the default body executes per BP3 apply (body_algorithmic)."""
+    return body_algorithmic(p, n)[3]
 
 
 class Clocks:
@@ -162,15 +171,14 @@ FP64_FMA_PER_SM_CLK = 2.0
 
 # DRAM bytes of one FP64 BP3 apply per order, from one ncu capture
 # (dram__bytes_read.sum, dram__bytes_write.sum) of `bench.py --profile
-# BP3:<p>:f64 --dofs 4e6` on a B300: (E, N, read, write) of the captured mesh.
-# The ratio to the algorithmic bytes (1.03-1.07; 0.79 at p = 1, whose body
-# reads the off-diagonal qdata and the line sums of the diagonal) is steady
-# across sizes (the bytes are qdata, indices and the two vectors, all
-# proportional to the mesh), so the full-size traffic is that ratio times the
-# full-size algorithmic bytes.
+# BP3:<p>:f64 --dofs 4e6` on a B300: (E, N, read, write) of the captured mesh,
+# with the default body.  The ratio to that body's algorithmic bytes
+# (body_algorithmic) is steady across sizes (the bytes are qdata or element
+# matrices, indices and the two vectors, all proportional to the mesh), so
+# the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 4138469120, 63885824),
-    2: (493039, 4019679, 1661260800, 46460416),
+    1: (3944312, 4019679, 1437170432, 23365632),
+    2: (493039, 4019679, 1682435584, 19062528),
     3: (148877, 4096000, 1021982720, 43140352),
     4: (59319, 3869893, 713128704, 31546112),
     5: (32768, 4173281, 638709248, 32124160),
@@ -181,9 +189,18 @@ APPLY_F64_DRAM = {
 
 
 def dram_ratio(p):
+    """Measured DRAM bytes over the default body's algorithmic bytes, or None
+    when no capture of the current body exists."""
+    if APPLY_F64_DRAM.get(p) is None:
+        return None
     E, N, rd, wr = APPLY_F64_DRAM[p]
     P, q = p + 1, p + 2
-    return (rd + wr) / (16 * N + 4 * E * P ** 3 + 48 * E * q ** 3)
+    if p in ELMAT_ORDERS:
+        P3 = P ** 3
+        alg = 16 * N + 4 * E * P3 + 8 * E * P3 * (P3 + 1) // 2
+    else:
+        alg = 16 * N + 4 * E * P ** 3 + 48 * E * q ** 3
+    return (rd + wr) / alg
 
 
 def cpu_baseline(work, iters, seconds, seed=0):
@@ -874,29 +891,36 @@ def main():
         a1.record(stream)
         torch.cuda.synchronize()
         t_apply = a0.elapsed_time(a1) / reps * 1e-3
-        N, E, by, fl = algorithmic(p, n)
+        N, E, by, fl = body_algorithmic(p, n)
+        _, _, _, fl_sf = algorithmic(p, n)
         per_p.append({"p": p, "N": N, "apply_ms": t_apply * 1e3,
                       "apply_gdofs": N / t_apply / 1e9,
+                      "body": "element matrices" if p in ELMAT_ORDERS else "sum factorization",
                       "apply_tflops": fl / t_apply / 1e12,
-                      "apply_hbm_gbs": by / t_apply / 1e9})
-        per_p[-1]["executed_tflops"] = executed_flops(p, n) / t_apply / 1e12
-        tot_time += t_apply; tot_flop += fl; tot_bytes += by
-        tot_exec += executed_flops(p, n)
-        tot_traffic += dram_ratio(p) * by
+                      "apply_hbm_gbs": by / t_apply / 1e9,
+                      "sum_factorization_flops_tflops": fl_sf / t_apply / 1e12})
+        per_p[-1]["executed_tflops"] = fl / t_apply / 1e12
+        tot_time += t_apply; tot_flop += fl_sf; tot_bytes += by
+        tot_exec += fl
+        r = dram_ratio(p)
+        tot_traffic = None if (r is None or tot_traffic is None) else tot_traffic + r * by
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     fp64_peak = fp64_peak_tflops(clocks.get("sm_mhz"))
-    achieved = tot_flop / tot_time / 1e12
+    achieved = tot_exec / tot_time / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak, "traffic": tot_traffic,
                 "traffic_note": "DRAM bytes of one sweep (one FP64 apply per order), ncu counters"
                                 " of a 4e6-DOF capture per order scaled by algorithmic bytes",
                 "algorithmic_bytes": tot_bytes,
-                "executed_tflops": tot_exec / tot_time / 1e12,
-                "executed_frac": tot_exec / tot_time / 1e12 / fp64_peak,
-                "executed_note": "achieved counts the formula's flops per element; the p = 1"
-                                 " trilinear body executes 39 % of them (executed_flops)",
-                "kernel": "FP64 fused apply (trilinear body p=1, slab body p=2, line body p>=3),"
+                "executed_tflops": achieved,
+                "executed_frac": achieved / fp64_peak,
+                "sum_factorization_flops_tflops": tot_flop / tot_time / 1e12,
+                "achieved_note": "flops each order's default body executes (element matrices at"
+                                 " p = 1, 2: 2 (P^3)^2 per element; sum factorization at p >= 3);"
+                                 " sum_factorization_flops_tflops counts every order with the"
+                                 " sum-factorized formula instead",
+                "kernel": "FP64 fused apply (element-matrix body p=1,2, line body p>=3),"
                           " all orders",
                 "hbm_achieved_gbs": tot_bytes / tot_time / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": tot_bytes / tot_time / 1e9 / hbm_peak,

@@ -151,6 +151,10 @@ fem_status fem_mesh_destroy(fem_mesh *mesh);
  *          kappa(x) = exp(sigma sqrt(2/M) sum_m cos(w_m . x + b_m)), a random
  *          Fourier feature draw of a Gaussian random field; the data D is
  *          multiplied by kappa at each physical quadrature point.
+ * Diffusion with a non-collocated rule at p = 1 and 2 also assembles the
+ * element matrices K_e = sum_q grad phi_a^T D grad phi_b in FP64 (and an
+ * FP32 copy with FEM_F32) for the element-matrix body: (P^3)(P^3 + 1)/2
+ * values per element, 36 at p = 1 and 378 at p = 2.
  * The mesh must outlive the operator.  Work goes to the mesh's stream. */
 fem_status fem_op_create(const fem_mesh *mesh, int kind, int quad, int q,
                          int ncomp, int prec, const double *rff_host, int M,
@@ -198,12 +202,13 @@ fem_status fem_op_rhs(fem_op *op, int which, double *b);
  * 1D operators and about 256, 128 or 512 threads per block, 3, 4, 5 = the
  * slab body (one thread per quadrature column) with the same three sizes,
  * 6 = the trilinear body (one thread per element; Gauss diffusion at p = 1
- * only).  The collocated mass operator (pointwise) has choice 0 only.
- * blocks_per_sm: resident blocks per SM (0 = the occupancy maximum).
- * Defaults (measured): FP64 diffusion 6 at p = 1 (Gauss), 3 for p = 2 and
- * the collocated operators, 0 from q = 5; FP32 diffusion 0, except p = 1
- * Gauss (6 with 2 blocks per SM at q = 3, 4 at q = 2); non-collocated mass
- * FP32 1, FP64 3 below q = 5, 0 up to q = 8, 1 from q = 9. */
+ * only), 7 = the element-matrix body (one thread per element with the
+ * operator's assembled element matrices; diffusion with a non-collocated
+ * rule at p = 1 and 2 only).  The collocated mass operator (pointwise) has
+ * choice 0 only.  blocks_per_sm: resident blocks per SM (0 = the occupancy
+ * maximum).  Defaults: the fastest choice of a sweep at 8e6 DOFs per order
+ * and operator type; among them 7 for Gauss diffusion at p = 1 (FP64 and
+ * FP32) and p = 2 (FP64). */
 typedef struct {
   int epb_choice;
   int blocks_per_sm;

@@ -5,6 +5,7 @@
 #pragma once
 #include "apply_lines.cuh"
 #include "apply_trilinear.cuh"
+#include "apply_elmat.cuh"
 
 namespace fem_apply {
 
@@ -134,14 +135,51 @@ int launch_trilinear(fem_op *op, const ApplyParams<T> &prm, int bps) {
   return FEM_OK;
 }
 
+// Assembled element matrices (Gauss diffusion, P = 2 and 3): one thread per
+// element.
+template <typename T, int P>
+int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
+  ElmatParams<T> ep;
+  ep.a = prm;
+  ep.E = op->E;
+  if constexpr (sizeof(T) == 8) ep.K = reinterpret_cast<const T *>(op->d_kel);
+  else ep.K = reinterpret_cast<const T *>(op->d_kel32);
+  if (!ep.K) {
+    fem_set_error("apply: the element-matrix body needs the operator's element matrices");
+    return FEM_EINVAL;
+  }
+  constexpr int NT = kElmatThreads;
+  auto kern = fem_apply_elmat_kernel<T, P>;
+  static FemKernelCache cache;
+  int &max_bps = cache.here();
+  if (max_bps < 0) {
+    int per_sm = 0;
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0));
+    max_bps = per_sm < 1 ? 1 : per_sm;
+  }
+  const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
+  const int64_t nblk = (prm.nsel + NT - 1) / NT;
+  int64_t grid = (int64_t)op->nsm * use;
+  if (grid > nblk) grid = nblk;
+  if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, NT, 0, op->stream()>>>(ep);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
 // Launch shape choice: 0..2 the line-based body with the three EPB
 // candidates, 3..5 the slab body, 6 the trilinear body (Gauss diffusion at
-// p = 1 only); the collocated mass operator (pointwise) has only the slab
-// body.
+// p = 1 only; the slab body's default elsewhere), 7 the element-matrix body
+// (Gauss diffusion at p = 1, 2); the collocated mass operator (pointwise)
+// has only the slab body.
 template <typename T, int P, int Q, int KIND, bool COLLOC>
 int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
   if constexpr (P == 2 && KIND == FEM_DIFFUSION && !COLLOC) {
     if (choice == 6) return launch_trilinear<T, Q>(op, prm, bps);
+  }
+  if constexpr ((P == 2 || P == 3) && KIND == FEM_DIFFUSION && !COLLOC) {
+    if (choice == 7) return launch_elmat<T, P>(op, prm, bps);
   }
   if constexpr (KIND == FEM_DIFFUSION || !COLLOC) {
     switch (choice) {

@@ -1,0 +1,89 @@
+// Element body of the diffusion apply with assembled element matrices, for
+// Gauss diffusion at P = 2 and 3 (p = 1, 2): one thread per element.
+//
+// The operator is still y = G^T (B^T D B) G x (section "libCEED": operator
+// decomposition); here the element block B^T D B is formed once at set-up,
+//   K_e[a][b] = sum_q grad phi_a(q)^T D(q) grad phi_b(q),
+// and the apply is the gather, the dense symmetric product y_e = K_e x_e and
+// the scatter-add.  The paper keeps full assembly for first and second
+// order and partial assembly for high order (section on the applications:
+// Laghos' two assembly options).  On B300 the crossover moves up: FP64 runs
+// at 1/64 of the FP32 rate and bounds the partially assembled apply, while
+// K_e costs (P^3)^2 FMAs per element (64 at p = 1, 729 at p = 2) against
+// about 370 and 1500 FP64 instructions of the sum-factorized bodies, and
+// its upper triangle (36 and 378 values) is no larger than the qdata those
+// bodies read.
+//
+// Layout: the upper triangle packed by rows (a <= b), stored entry-major
+// [P^3 (P^3 + 1) / 2][E] (fem_op::d_kel): the 32 elements of a warp load
+// each entry in one coalesced access.  x_e and y_e stay in registers.
+#pragma once
+#include "apply_kernel.cuh"
+
+namespace fem_apply {
+
+template <typename T>
+struct ElmatParams {
+  ApplyParams<T> a;
+  const T *K;     // [P^3 (P^3 + 1) / 2][E]
+  int64_t E;      // element stride of K (all elements of the operator)
+};
+
+constexpr int kElmatThreads = 128;
+
+// Element e: y += K_e x_e (every component) and this thread's share of x.y.
+template <typename T, int P>
+__device__ __forceinline__ void elmat_element(const ApplyParams<T> &prm, const T *__restrict__ K,
+                                              int64_t E, int64_t e, DotAcc<T> &dl) {
+  constexpr int P3 = P * P * P;
+  int id[P3];
+  const int32_t *en = prm.elem_nodes + e * P3;
+#pragma unroll
+  for (int a = 0; a < P3; a++) id[a] = en[a];
+  for (int c = 0; c < prm.ncomp; c++) {
+    const T *xc = prm.x + c * prm.N;
+    T *yc = prm.y + c * prm.N;
+    T x[P3], y[P3];
+#pragma unroll
+    for (int a = 0; a < P3; a++) {
+      x[a] = gather_load(&xc[id[a]], prm.x_l2_only);
+      y[a] = T(0);
+    }
+    // the entries in their packed order: K_e is streamed once per apply
+    // (evict-first loads keep x and y in L2)
+    const T *kp = K + e;
+#pragma unroll
+    for (int a = 0; a < P3; a++) {
+#pragma unroll
+      for (int b = a; b < P3; b++) {
+        const T kv = __ldcs(kp);
+        kp += E;
+        y[a] = fma(kv, x[b], y[a]);
+        if (b != a) y[b] = fma(kv, x[a], y[b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < P3; a++) {
+      atomic_add(&yc[id[a]], y[a]);
+      dl.add(y[a], x[a]);
+    }
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kElmatThreads) fem_apply_elmat_kernel(const ElmatParams<T> ep) {
+  const ApplyParams<T> &prm = ep.a;
+  if (apply_skipped(prm)) return;
+  DotAcc<T> dl;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k_el = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k_el < prm.nsel; k_el += stride)
+    elmat_element<T, P>(prm, ep.K, ep.E, prm.list ? (int64_t)prm.list[k_el] : k_el, dl);
+  if (prm.dot_out) {
+    double v[1] = {dl.get()};
+    __shared__ double tot[1];
+    if (fem_grid_sum<1>(v, prm.partials, prm.counter, tot) && threadIdx.x == 0)
+      *prm.dot_out = tot[0];
+  }
+}
+
+}  // namespace fem_apply

@@ -41,6 +41,65 @@ __global__ void qdata_line_sums_kernel(const double *qd, int64_t E, int Q, doubl
   }
 }
 
+// Element matrices of Gauss diffusion at P = 2, 3 (fem_op::d_kel):
+//   K_e[a][b] = sum_q grad phi_a(q)^T D(q) grad phi_b(q),
+// grad phi_a(q) = (G_i B_j B_k, B_i G_j B_k, B_i B_j G_k) at node a =
+// (ax, ay, az), point q = (i, j, k), with the 1D tables taken at those
+// indices.  One thread per (element, row a); per point, w = D grad phi_a and
+// then w . grad phi_b for every b, factored direction by direction.
+struct ElmatTabs {
+  double B[FEM_MAX_Q * 3], G[FEM_MAX_Q * 3];   // [k][a], P <= 3
+};
+
+template <int P>
+__global__ void elmat_setup_kernel(const double *qd, int64_t E, int Q, const ElmatTabs t, double *K) {
+  constexpr int P3 = P * P * P;
+  const int Q2 = Q * Q, Q3 = Q2 * Q;
+  const int64_t total = E * P3;
+  for (int64_t th = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; th < total;
+       th += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = th / P3;
+    const int a = (int)(th - e * P3);
+    const int ax = a % P, ay = (a / P) % P, az = a / (P * P);
+    double row[P3];
+#pragma unroll
+    for (int b = 0; b < P3; b++) row[b] = 0.0;
+    const double *q = qd + e * 6 * (int64_t)Q3;
+    for (int k = 0; k < Q; k++)
+      for (int j = 0; j < Q; j++)
+        for (int i = 0; i < Q; i++) {
+          const int pt = i + Q * j + Q2 * k;
+          const double ga0 = t.G[i * P + ax] * t.B[j * P + ay] * t.B[k * P + az];
+          const double ga1 = t.B[i * P + ax] * t.G[j * P + ay] * t.B[k * P + az];
+          const double ga2 = t.B[i * P + ax] * t.B[j * P + ay] * t.G[k * P + az];
+          const double d00 = q[pt], d11 = q[Q3 + pt], d22 = q[2 * Q3 + pt];
+          const double d12 = q[3 * Q3 + pt], d02 = q[4 * Q3 + pt], d01 = q[5 * Q3 + pt];
+          const double w0 = d00 * ga0 + d01 * ga1 + d02 * ga2;
+          const double w1 = d01 * ga0 + d11 * ga1 + d12 * ga2;
+          const double w2 = d02 * ga0 + d12 * ga1 + d22 * ga2;
+          // w . grad phi_b = (w0 G_i[bx] B_j[by] + w1 B_i[bx] G_j[by]) B_k[bz]
+          //                + w2 B_i[bx] B_j[by] G_k[bz]
+#pragma unroll
+          for (int bx = 0; bx < P; bx++) {
+            const double u0 = w0 * t.G[i * P + bx], u1 = w1 * t.B[i * P + bx], u2 = w2 * t.B[i * P + bx];
+#pragma unroll
+            for (int by = 0; by < P; by++) {
+              const double s01 = u0 * t.B[j * P + by] + u1 * t.G[j * P + by];
+              const double s2 = u2 * t.B[j * P + by];
+#pragma unroll
+              for (int bz = 0; bz < P; bz++)
+                row[bx + P * by + P * P * bz] += s01 * t.B[k * P + bz] + s2 * t.G[k * P + bz];
+            }
+          }
+        }
+    // upper triangle of row a: packed entries a*P3 - a(a-1)/2 + (b - a)
+    const int64_t start = (int64_t)a * P3 - (int64_t)a * (a - 1) / 2 - a;
+#pragma unroll
+    for (int b = 0; b < P3; b++)
+      if (b >= a) K[(start + b) * E + e] = row[b];
+  }
+}
+
 __global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -235,12 +294,12 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   // Default launch shapes: the fastest choice (fem_apply_choices) of a
   // sweep of every choice at 8e6 DOFs on a B300, per P = p + 1 (index P - 2):
   // BP3 (Gauss q = p + 2), BP5 (collocated) and BP1 (Gauss mass).  Among
-  // them: the trilinear body (6) for Gauss diffusion at p = 1 (FP64 2.4x the
-  // slab body; FP32 at q = 3 with two blocks per SM), the slab body for FP64
-  // at p <= 2 and for most collocated FP64 orders, the line body elsewhere,
-  // often with half the default elements per block (1).
-  static const int kDiffF32[8] = {6, 1, 1, 0, 1, 0, 0, 1};
-  static const int kDiffF64[8] = {6, 3, 1, 0, 0, 1, 0, 2};
+  // them: the element-matrix body (7) for Gauss diffusion at p = 1 (FP64
+  // 6.5x the trilinear body at 5e7 DOFs, FP32 3.2x) and in FP64 at p = 2
+  // (4.8x the slab body), the slab body for most collocated FP64 orders, the
+  // line body elsewhere, often with half the default elements per block (1).
+  static const int kDiffF32[8] = {7, 1, 1, 0, 1, 0, 0, 1};
+  static const int kDiffF64[8] = {7, 7, 1, 0, 0, 1, 0, 2};
   static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
   static const int kCollF64[8] = {4, 3, 3, 4, 3, 3, 4, 2};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
@@ -249,11 +308,6 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   if (kind == FEM_DIFFUSION && !op->colloc) {
     op->tune_epb[FEM_F32] = kDiffF32[ip];
     op->tune_epb[FEM_F64] = kDiffF64[ip];
-    if (P == 2 && Q == 3) {
-      // trilinear FP32 at q = 3 with two blocks per SM (1.28 vs 1.29 ms at
-      // the occupancy maximum, 8e6 DOFs)
-      op->tune_bps[FEM_F32] = 2;
-    }
   } else if (kind == FEM_DIFFUSION) {
     op->tune_epb[FEM_F32] = kCollF32[ip];
     op->tune_epb[FEM_F64] = kCollF64[ip];
@@ -314,6 +368,24 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
       if (ns > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qsum, op->d_qsum32, (int64_t)ns);
     }
   }
+  if (fem_has_elmat(kind, op->colloc, P)) {
+    // element matrices for the element-matrix body (launch choice 7)
+    const int P3 = P * P * P;
+    const size_t nk = (size_t)op->E * (size_t)(P3 * (P3 + 1) / 2);
+    if ((rc = dev_alloc(&op->d_kel, nk, &op->bytes))) { fem_op_destroy(op); return rc; }
+    ElmatTabs et;
+    memset(&et, 0, sizeof(et));
+    memcpy(et.B, op->tab.B, sizeof(double) * Q * P);
+    memcpy(et.G, op->tab.G, sizeof(double) * Q * P);
+    if (nk > 0) {
+      if (P == 2) elmat_setup_kernel<2><<<148 * 8, 128, 0, s>>>(op->d_qdata, op->E, Q, et, op->d_kel);
+      else elmat_setup_kernel<3><<<148 * 8, 128, 0, s>>>(op->d_qdata, op->E, Q, et, op->d_kel);
+    }
+    if (prec == FEM_F32) {
+      if ((rc = dev_alloc(&op->d_kel32, nk, &op->bytes))) { fem_op_destroy(op); return rc; }
+      if (nk > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_kel, op->d_kel32, (int64_t)nk);
+    }
+  }
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -333,6 +405,7 @@ extern "C" fem_status fem_op_destroy(fem_op *op) {
   if (op->d_B32) cudaFree(op->d_B32 - TAB_B);
   cudaFree(op->d_qdata); cudaFree(op->d_qdata32); cudaFree(op->d_diag); cudaFree(op->d_rff);
   cudaFree(op->d_qsum); cudaFree(op->d_qsum32);
+  cudaFree(op->d_kel); cudaFree(op->d_kel32);
   cudaFree(op->d_partials); cudaFree(op->d_counter);
   delete op;
   return FEM_OK;

@@ -90,6 +90,11 @@ struct fem_op {
   // over j of D11 at (i, k) (i + Q k), over k of D22 at (i, j) (i + Q j)
   double *d_qsum = nullptr;
   float *d_qsum32 = nullptr;
+  // Gauss diffusion at P = 2 and 3 only: the element matrices
+  // K_e = sum_q grad phi_a^T D grad phi_b, upper triangle packed by rows
+  // (a <= b), entry-major [P^3 (P^3 + 1) / 2][E]
+  double *d_kel = nullptr;
+  float *d_kel32 = nullptr;
   double *d_diag = nullptr;       // [N] scalar diagonal
   double *d_rff = nullptr;        // [M][4]
   int M = 0;
@@ -156,11 +161,19 @@ int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32
                                const int *skip = nullptr);
 // Launch shape choices of an operator's apply: 0..2 the line-based body
 // (elements per block default, half, double), 3..5 the slab body, 6 the
-// trilinear body (Gauss diffusion at p = 1); the collocated mass operator
-// (pointwise) has one.
+// trilinear body (Gauss diffusion at p = 1; at p = 2 the slab body's
+// default again), 7 the element-matrix body (Gauss diffusion at p = 1, 2);
+// the collocated mass operator (pointwise) has one.
+inline bool fem_has_elmat(int kind, bool colloc, int P) {
+  return kind == FEM_DIFFUSION && !colloc && (P == 2 || P == 3);
+}
 inline int fem_apply_choices(const fem_op *op) {
-  if (op->kind == FEM_DIFFUSION && !op->colloc && op->P == 2) return 7;
+  if (fem_has_elmat(op->kind, op->colloc, op->P)) return 8;
   return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
+}
+// Choice c is a valid launch shape of op's apply (6 exists at P = 2 only).
+inline bool fem_apply_choice_valid(const fem_op *op, int c) {
+  return c >= 0 && c < fem_apply_choices(op) && !(c == 6 && op->P != 2);
 }
 // ---- p-multigrid internals used by the refined flexible CG (pmg.cu)
 struct fem_pmg;

@@ -101,8 +101,8 @@ int launch(fem_op *op, int prec, void *x, void *y, int choice, int bps) {
 
 extern "C" fem_status fem_op_set_launch_shape(fem_op *op, int prec, int epb_choice,
                                               int blocks_per_sm) {
-  if (!op || (prec != FEM_F64 && prec != FEM_F32) || epb_choice < 0 ||
-      epb_choice >= n_choices(op) || blocks_per_sm < 0) {
+  if (!op || (prec != FEM_F64 && prec != FEM_F32) || !fem_apply_choice_valid(op, epb_choice) ||
+      blocks_per_sm < 0) {
     fem_set_error("fem_op_set_launch_shape: invalid arguments");
     return FEM_EINVAL;
   }
@@ -127,7 +127,7 @@ extern "C" fem_status fem_op_autotune(fem_op *op, int prec, const char *cache_pa
     entries = read_entries(cache_path);
     int c, b;
     double us;
-    if (lookup(entries, key, &c, &b, &us) && c >= 0 && c < n_choices(op) && b >= 0) {
+    if (lookup(entries, key, &c, &b, &us) && fem_apply_choice_valid(op, c) && b >= 0) {
       op->tune_epb[prec] = c;
       op->tune_bps[prec] = b;
       if (res) { res->epb_choice = c; res->blocks_per_sm = b; res->us = us; res->from_cache = 1; res->candidates = 0; }
@@ -152,6 +152,7 @@ extern "C" fem_status fem_op_autotune(fem_op *op, int prec, const char *cache_pa
   double best = 1e300;
   int best_c = 0, best_b = 0, ncand = 0;
   for (int c = 0; c < n_choices(op) && rc == FEM_OK; c++) {
+    if (!fem_apply_choice_valid(op, c)) continue;
     for (int bps : kBpsCandidates) {
       // warm-up (also sets the kernel attributes)
       for (int w = 0; w < 2 && rc == FEM_OK; w++) rc = launch(op, prec, x, y, c, bps);

@@ -235,6 +235,57 @@ def test_trilinear_body_in_cg_and_only_where_valid():
             op2.set_launch_shape(fem.F64, 6, 0)
 
 
+# ---------------------------------------------------------------- element-matrix body
+@pytest.mark.parametrize("p,q,ncomp", [(1, 3, 1), (1, 2, 3), (2, 4, 1), (2, 3, 3)])
+def test_element_matrix_body_matches_oracle(p, q, ncomp):
+    # Gauss diffusion at p = 1, 2, one thread per element with the assembled
+    # K_e (launch choice 7): 9^3 / 6^3 elements = several blocks of 128
+    # threads with a ragged tail, shuffled order, both precisions
+    n = 9 if p == 1 else 6
+    m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=13, shuffle_seed=5)
+    gm = fem.Mesh(m)
+    op = fem.Operator(gm, fem.DIFFUSION, fem.GAUSS, q, ncomp=ncomp, prec=fem.F32)
+    orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, q, ncomp=ncomp)
+    for prec, tol in ((fem.F64, TOL64), (fem.F32, 1e-5)):
+        for bps in (1, 0):
+            op.set_launch_shape(prec, 7, bps)
+            for x in inputs(m, ncomp, seed=q + 10 * p):
+                xt = torch.from_numpy(x).cuda()
+                if prec == fem.F64:
+                    y = op.apply(xt).cpu().numpy()
+                else:
+                    y = op.apply_f32(xt.float()).double().cpu().numpy()
+                assert rel(y, orc.apply(x)) <= tol, (prec, bps)
+    # a listed subset of elements, and the empty list
+    op.set_launch_shape(fem.F64, 7, 0)
+    x = inputs(m, ncomp)[0]
+    sel = np.random.default_rng(3).choice(m["E"], size=m["E"] // 3, replace=False).astype(np.int32)
+    y = op.apply_elements(torch.from_numpy(sel).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, orc.apply(x, elems=sel)) <= TOL64
+    y0 = op.apply_elements(torch.zeros(0, dtype=torch.int32, device="cuda"),
+                           torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.all(y0 == 0.0)
+
+
+def test_element_matrix_body_in_cg_and_only_where_valid():
+    # the fused p^T A p of the element-matrix body drives CG to the oracle's
+    # iteration count and solution (the default body at p = 1, 2 in FP64)
+    for p, n in ((1, 7), (2, 4)):
+        m, gm, op, orc = make("BP3", n, p, shuffle=6)
+        op.set_launch_shape(fem.F64, 7, 0)
+        b = fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=5)
+        xr, itr, _ = oracle.pcg(orc, b, m["dirichlet"], rtol=1e-10)
+        x = torch.zeros(m["N"], dtype=torch.float64, device="cuda")
+        st = op.cg(torch.from_numpy(b).cuda(), x, precond=fem.PC_JACOBI, rtol=1e-10)
+        assert st["status"] == "FEM_OK" and abs(st["iterations"] - itr) <= 2, (p, st, itr)
+        assert rel(x.cpu().numpy(), xr) <= 1e-8
+    # choice 7 exists for diffusion with a non-collocated rule at p = 1, 2 only
+    for name, p in (("BP3", 3), ("BP5", 1), ("BP5", 2), ("BP1", 1)):
+        _, _, op2, _ = make(name, 2, p)
+        with pytest.raises(fem.FemError):
+            op2.set_launch_shape(fem.F64, 7, 0)
+
+
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_cg_zero_guess_ignores_x_and_matches_explicit_zero(use_graph):
     m, gm, op, orc = make("BP3", 4, 2, seed=6)

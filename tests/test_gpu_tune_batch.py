@@ -31,7 +31,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("name,p,n", [("BP3", 3, 3), ("BP5", 7, 2), ("BP3", 8, 2), ("BP1", 3, 3),
-                                      ("BP1", 8, 2), ("BP1", 1, 5), ("BP3", 1, 6)])
+                                      ("BP1", 8, 2), ("BP1", 1, 5), ("BP3", 1, 6), ("BP3", 2, 5)])
 @pytest.mark.parametrize("prec", [fem.F64, fem.F32])
 def test_every_launch_shape_matches_oracle(name, p, n, prec):
     kind, ncomp, quad, dq = fem.BAKE_OFF[name]
@@ -42,9 +42,11 @@ def test_every_launch_shape_matches_oracle(name, p, n, prec):
     x = np.random.default_rng(1).uniform(-1, 1, m["N"])
     ref = orc.apply(x)
     tol = 1e-12 if prec == fem.F64 else 1e-5
-    # 0-2 line-based body, 3-5 slab body, 6 trilinear body (Gauss diffusion, p = 1)
-    nchoice = 7 if (p == 1 and kind == fem.DIFFUSION) else 6
-    for choice in range(nchoice):
+    # 0-2 line-based body, 3-5 slab body, 6 trilinear body (Gauss diffusion,
+    # p = 1), 7 element-matrix body (Gauss diffusion, p = 1, 2)
+    gauss_diff = kind == fem.DIFFUSION and quad == fem.GAUSS
+    choices = list(range(6)) + ([6] if gauss_diff and p == 1 else []) + ([7] if gauss_diff and p <= 2 else [])
+    for choice in choices:
         for bps in (1, 2, 0):
             op.set_launch_shape(prec, choice, bps)
             if prec == fem.F64:
