@@ -6,13 +6,13 @@
 //   K_e[a][b] = sum_q grad phi_a(q)^T D(q) grad phi_b(q),
 // and the apply is the gather, the dense symmetric product y_e = K_e x_e and
 // the scatter-add.  The paper keeps full assembly for first and second
-// order and partial assembly for high order (section on the applications:
-// Laghos' two assembly options).  On B300 the crossover moves up: FP64 runs
-// at 1/64 of the FP32 rate and bounds the partially assembled apply, while
-// K_e costs (P^3)^2 FMAs per element (64 at p = 1, 729 at p = 2) against
-// about 370 and 1500 FP64 instructions of the sum-factorized bodies, and
-// its upper triangle (36 and 378 values) is no larger than the qdata those
-// bodies read.
+// order and partial assembly for high order (section "Miniapps": Laghos'
+// full and partial assembly options), and on B300 the FP64 apply agrees:
+// FP64 runs at 1/64 of the FP32 rate and bounds the partially assembled
+// apply, while K_e costs (P^3)^2 FMAs per element (64 at p = 1, 729 at
+// p = 2) against about 370 and 1500 FP64 instructions of the sum-factorized
+// bodies, and its upper triangle (36 and 378 values) is no larger than the
+// qdata those bodies read.
 //
 // Layout: the upper triangle packed by rows (a <= b), stored entry-major
 // [P^3 (P^3 + 1) / 2][E] (fem_op::d_kel): the 32 elements of a warp load
