@@ -100,6 +100,26 @@ __global__ void elmat_setup_kernel(const double *qd, int64_t E, int Q, const Elm
   }
 }
 
+__global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n);
+
+// The trilinear body's line sums (fem_op::d_qsum), made when that body is
+// first selected: the trilinear body applies the diagonal of D once per line.
+int ensure_qsum(fem_op *op) {
+  if (op->d_qsum || !(op->kind == FEM_DIFFUSION && !op->colloc && op->P == 2)) return FEM_OK;
+  const int Q = op->Q;
+  const size_t ns = (size_t)op->E * 3 * Q * Q;
+  cudaStream_t s = op->stream();
+  int rc;
+  if ((rc = dev_alloc(&op->d_qsum, ns, &op->bytes))) return rc;
+  if (ns > 0) qdata_line_sums_kernel<<<148 * 8, 256, 0, s>>>(op->d_qdata, op->E, Q, op->d_qsum);
+  if (op->d_qdata32) {
+    if ((rc = dev_alloc(&op->d_qsum32, ns, &op->bytes))) return rc;
+    if (ns > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qsum, op->d_qsum32, (int64_t)ns);
+  }
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
 __global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -107,6 +127,8 @@ __global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n) {
 }
 
 }  // namespace
+
+int fem_ensure_qsum(fem_op *op) { return ensure_qsum(op); }
 
 extern "C" fem_status fem_mesh_create(int p, int64_t N, int64_t E, const int32_t *en,
                                       const double *xyz, const uint8_t *dir, void *stream,
@@ -358,15 +380,8 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
     if ((rc = dev_alloc(&op->d_qdata32, nq, &op->bytes))) { fem_op_destroy(op); return rc; }
     if (nq > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qdata, op->d_qdata32, (int64_t)nq);
   }
-  if (kind == FEM_DIFFUSION && !op->colloc && P == 2) {
-    // the trilinear body applies the diagonal of D once per line
-    const size_t ns = (size_t)op->E * 3 * Q * Q;
-    if ((rc = dev_alloc(&op->d_qsum, ns, &op->bytes))) { fem_op_destroy(op); return rc; }
-    if (ns > 0) qdata_line_sums_kernel<<<148 * 8, 256, 0, s>>>(op->d_qdata, op->E, Q, op->d_qsum);
-    if (prec == FEM_F32) {
-      if ((rc = dev_alloc(&op->d_qsum32, ns, &op->bytes))) { fem_op_destroy(op); return rc; }
-      if (ns > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qsum, op->d_qsum32, (int64_t)ns);
-    }
+  if (op->tune_epb[FEM_F64] == 6 || op->tune_epb[FEM_F32] == 6) {
+    if ((rc = fem_ensure_qsum(op))) { fem_op_destroy(op); return rc; }
   }
   if (fem_has_elmat(kind, op->colloc, P)) {
     // element matrices for the element-matrix body (launch choice 7)

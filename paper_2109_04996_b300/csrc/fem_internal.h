@@ -85,7 +85,8 @@ struct fem_op {
   float *d_B32 = nullptr, *d_Dq32 = nullptr;
   double *d_qdata = nullptr;      // [E][nd][Q^3]
   float *d_qdata32 = nullptr;     // FP32 copy (prec == FEM_F32)
-  // trilinear Gauss diffusion only (P = 2): line sums of the diagonal qdata
+  // trilinear Gauss diffusion only (P = 2), made when the trilinear body is
+  // first selected (fem_ensure_qsum): line sums of the diagonal qdata
   // components, [E][3][Q^2]: sum over i of D00 at (j, k) (index j + Q k),
   // over j of D11 at (i, k) (i + Q k), over k of D22 at (i, j) (i + Q j)
   double *d_qsum = nullptr;
@@ -171,6 +172,10 @@ inline int fem_apply_choices(const fem_op *op) {
   if (fem_has_elmat(op->kind, op->colloc, op->P)) return 8;
   return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
 }
+// Allocate and compute the trilinear body's line sums if op has none yet
+// (capi.cu); called where choice 6 is selected, outside stream capture.
+int fem_ensure_qsum(fem_op *op);
+
 // Choice c is a valid launch shape of op's apply (6 exists at P = 2 only).
 inline bool fem_apply_choice_valid(const fem_op *op, int c) {
   return c >= 0 && c < fem_apply_choices(op) && !(c == 6 && op->P != 2);

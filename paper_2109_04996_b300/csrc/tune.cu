@@ -106,6 +106,10 @@ extern "C" fem_status fem_op_set_launch_shape(fem_op *op, int prec, int epb_choi
     fem_set_error("fem_op_set_launch_shape: invalid arguments");
     return FEM_EINVAL;
   }
+  if (epb_choice == 6) {
+    const int rc = fem_ensure_qsum(op);
+    if (rc) return rc;
+  }
   op->tune_epb[prec] = epb_choice;
   op->tune_bps[prec] = blocks_per_sm;
   return FEM_OK;
@@ -128,6 +132,10 @@ extern "C" fem_status fem_op_autotune(fem_op *op, int prec, const char *cache_pa
     int c, b;
     double us;
     if (lookup(entries, key, &c, &b, &us) && fem_apply_choice_valid(op, c) && b >= 0) {
+      if (c == 6) {
+        const int rc = fem_ensure_qsum(op);
+        if (rc) return rc;
+      }
       op->tune_epb[prec] = c;
       op->tune_bps[prec] = b;
       if (res) { res->epb_choice = c; res->blocks_per_sm = b; res->us = us; res->from_cache = 1; res->candidates = 0; }
@@ -153,6 +161,7 @@ extern "C" fem_status fem_op_autotune(fem_op *op, int prec, const char *cache_pa
   int best_c = 0, best_b = 0, ncand = 0;
   for (int c = 0; c < n_choices(op) && rc == FEM_OK; c++) {
     if (!fem_apply_choice_valid(op, c)) continue;
+    if (c == 6 && (rc = fem_ensure_qsum(op))) break;
     for (int bps : kBpsCandidates) {
       // warm-up (also sets the kernel attributes)
       for (int w = 0; w < 2 && rc == FEM_OK; w++) rc = launch(op, prec, x, y, c, bps);
