@@ -506,7 +506,8 @@ fem_status fem_precond_create_pmg(fem_pmg *pmg, fem_precond **out);
  * cudaMalloc's implicit device-wide synchronization is not acceptable.
  *
  * Same arguments, arithmetic and results as fem_cg_solve (FEM_PC_NONE or
- * FEM_PC_JACOBI; launches are host-driven, no CUDA graph), but the CG
+ * FEM_PC_JACOBI; opts->zero_guess is honoured as there; launches are
+ * host-driven, no CUDA graph, so opts->use_graph is ignored), but the CG
  * workspace (five vectors, reduction partials, scalars) lives in one fixed
  * file-scope device array of the library instead of cudaMalloc'd buffers, so
  * the call allocates nothing.  The array holds 5 * FEM_NOALLOC_MAX_N doubles

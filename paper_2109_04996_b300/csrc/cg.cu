@@ -468,7 +468,7 @@ extern "C" fem_status fem_cg_solve_noalloc(fem_op *op, const double *b, double *
   cg_dinv_kernel<<<grid_for(n), kThreads, 0, s>>>(op->d_diag, op->mesh->d_dirichlet, op->N, n,
                                                   o->precond, dinv);
   FEM_CHECK_LAUNCH();
-  rc = launch_prologue(op, c, s);
+  rc = launch_prologue(op, c, s, o->zero_guess ? 1 : 0);
   if (rc) return rc;
   for (int it = 0; it < o->maxit; it++) {
     rc = launch_body(op, c, s);
