@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--learned-n", type=int, default=64, help="elements per direction, kappa BP3 p=4")
     ap.add_argument("--profile", default=None,
-                    help="only time the apply of one operator, e.g. BP5:7:f32 (problem:order:prec)"
+                    help="only time the apply of one operator, e.g. BP5:7:f32 (problem:order:prec"
+                         "[:launch choice])"
                          " on a mesh of --dofs nodes, or PMG:4:f32 for p-multigrid V-cycles,"
                          " BATCH:256:8 for the persistent batch kernel;"
                          " for profilers")
@@ -102,11 +103,6 @@ def body_algorithmic(p, n):
         by = 16 * N + 4 * E * P3 + 8 * E * P3 * (P3 + 1) // 2
         fl = E * (2 * P3 * P3 + 2 * P3)
     return N, E, by, fl
-
-
-def executed_flops(p, n):
-    """FP64 flops the default body executes per BP3 apply (body_algorithmic)."""
-    return body_algorithmic(p, n)[3]
 
 
 class Clocks:
@@ -160,31 +156,22 @@ def measured_peaks():
         return {}
 
 
-def fp64_peak_tflops(sm_mhz):
-    """FP64 FMA peak derived from unit counts and clock: 148 SMs x 2 FP64 FMA
-    per SM per clock x 2 flops x the SM clock (1.20 TFLOP/s at 2032 MHz; the
-    B300 nominal is 1.25 TFLOP/s)."""
-    return 148 * FP64_FMA_PER_SM_CLK * 2 * (sm_mhz or 2032.0) * 1e6 / 1e12
-
-
-FP64_FMA_PER_SM_CLK = 2.0
-
 # DRAM bytes of one FP64 BP3 apply per order, from one ncu capture
 # (dram__bytes_read.sum, dram__bytes_write.sum) of `bench.py --profile
 # BP3:<p>:f64 --dofs 4e6` on a B300: (E, N, read, write) of the captured mesh,
-# with the default body.  The ratio to that body's algorithmic bytes
+# with the default (double-word) body.  The ratio to that body's algorithmic bytes
 # (body_algorithmic) is steady across sizes (the bytes are qdata or element
 # matrices, indices and the two vectors, all proportional to the mesh), so
 # the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 1437170432, 23365632),
-    2: (493039, 4019679, 1682435584, 19062528),
-    3: (148877, 4096000, 1021982720, 43140352),
-    4: (59319, 3869893, 713128704, 31546112),
-    5: (32768, 4173281, 638709248, 32124160),
-    6: (17576, 3869893, 522320384, 29230080),
-    7: (12167, 4251528, 524337408, 31831296),
-    8: (8000, 4173281, 474709504, 29166592),
+    1: (3944312, 4019679, 1356422912, 23052800),
+    2: (493039, 4019679, 1613657600, 18308096),
+    3: (148877, 4096000, 997886976, 32472576),
+    4: (59319, 3869893, 706749696, 29074176),
+    5: (32768, 4173281, 634727168, 31795456),
+    6: (17576, 3869893, 518107904, 27657216),
+    7: (12167, 4251528, 518893056, 30707712),
+    8: (8000, 4173281, 474284032, 28973824),
 }
 
 
@@ -270,19 +257,22 @@ def run_reference(args):
         return
     work = workload(args)
     base = cpu_baseline(work, args.iters, max(2.0, args.cpu_seconds / 3))
-    ms = 0.0
     steps = []
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
         b = cpu_baseline(work, args.iters, max(1.0, args.cpu_seconds / 5), seed=s)
         if s >= args.warmup:
             steps.append(b["value"])
-        ms += 0.0 * (time.perf_counter() - t0)
     val = float(np.median(steps))
     N_tot = sum(algorithmic(p, n)[0] for p, n in work)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GDOF/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": N_tot * args.iters / (val * 1e9) * 1e3,
+            "extrapolated": True,
+            "extrapolation_note": "value and ms_per_step are extrapolated, not timed over a whole"
+                                  " step: each step times the oracle's brute-force element apply"
+                                  " on a bounded sample of every order's elements (the sample"
+                                  " field) and scales that rate to the step's DOF-iterations;"
+                                  " a whole step would take hours on the host",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args, work),
             "cpu_baseline": dict(base, value=val),
@@ -712,7 +702,9 @@ def run_profile(args):
         print(json.dumps({"profile": args.profile, "problems": count,
                           "dofs": sum(o.n for o in ops), "tune": r}))
         return
-    name, p, prec = args.profile.split(":")
+    fields = args.profile.split(":")
+    name, p, prec = fields[:3]
+    choice = int(fields[3]) if len(fields) > 3 else None   # launch choice (default: the operator's)
     p = int(p)
     n = fem_inputs.bp3_mesh_n(args.dofs, p)
     if name == "PMG":
@@ -742,6 +734,8 @@ def run_profile(args):
     m = fem_inputs.box_mesh(n, p, perturb=0.1, seed=900)
     gm = fem.Mesh(m)
     op = fem.Operator.bake_off(gm, name, prec=fem.F32)
+    if choice is not None:
+        op.set_launch_shape(fem.F32 if prec == "f32" else fem.F64, choice, 0)
     nc = op.ncomp
     x = torch.from_numpy(np.random.default_rng(0).uniform(-1, 1, nc * m["N"])).cuda()
     if prec == "f32":
@@ -895,37 +889,37 @@ def main():
         _, _, _, fl_sf = algorithmic(p, n)
         per_p.append({"p": p, "N": N, "apply_ms": t_apply * 1e3,
                       "apply_gdofs": N / t_apply / 1e9,
-                      "body": "element matrices" if p in ELMAT_ORDERS else "sum factorization",
-                      "apply_tflops": fl / t_apply / 1e12,
+                      "body": ("double-word element matrices" if p in ELMAT_ORDERS
+                               else "double-word sum factorization"),
                       "apply_hbm_gbs": by / t_apply / 1e9,
+                      "operator_tflops": fl / t_apply / 1e12,
                       "sum_factorization_flops_tflops": fl_sf / t_apply / 1e12})
-        per_p[-1]["executed_tflops"] = fl / t_apply / 1e12
         tot_time += t_apply; tot_flop += fl_sf; tot_bytes += by
         tot_exec += fl
         r = dram_ratio(p)
         tot_traffic = None if (r is None or tot_traffic is None) else tot_traffic + r * by
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
-    fp64_peak = fp64_peak_tflops(clocks.get("sm_mhz"))
-    achieved = tot_exec / tot_time / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": tot_traffic,
+    achieved = tot_bytes / tot_time / 1e9
+    sf_orders = [d for d in per_p if d["p"] >= 3]
+    sf_bytes = sum(body_algorithmic(d["p"], dict((p, n) for p, n in work)[d["p"]])[2] for d in sf_orders)
+    sf_time = sum(d["apply_ms"] for d in sf_orders) * 1e-3
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": tot_traffic,
                 "traffic_note": "DRAM bytes of one sweep (one FP64 apply per order), ncu counters"
-                                " of a 4e6-DOF capture per order scaled by algorithmic bytes",
+                                " of a 4e6-DOF capture per order scaled by algorithmic bytes;"
+                                " null when no capture of the current bodies exists",
                 "algorithmic_bytes": tot_bytes,
-                "executed_tflops": achieved,
-                "executed_frac": achieved / fp64_peak,
+                "achieved_note": "algorithmic bytes of one FP64 apply per order (x, y, element"
+                                 " indices, qdata -- or the packed element matrices at p = 1, 2)"
+                                 " over the summed event-timed apply durations",
+                "sum_factorized_orders_frac": (sf_bytes / sf_time / 1e9 / hbm_peak
+                                               if sf_time > 0 else None),
+                "operator_tflops": tot_exec / tot_time / 1e12,
                 "sum_factorization_flops_tflops": tot_flop / tot_time / 1e12,
-                "achieved_note": "flops each order's default body executes (element matrices at"
-                                 " p = 1, 2: 2 (P^3)^2 per element; sum factorization at p >= 3);"
-                                 " sum_factorization_flops_tflops counts every order with the"
-                                 " sum-factorized formula instead",
-                "kernel": "FP64 fused apply (element-matrix body p=1,2, line body p>=3),"
-                          " all orders",
-                "hbm_achieved_gbs": tot_bytes / tot_time / 1e9, "hbm_peak_gbs": hbm_peak,
-                "hbm_frac": tot_bytes / tot_time / 1e9 / hbm_peak,
-                "peak_source": "FP64 peak = 148 SMs x 2 FMA/clk x 2 flop x median SM clock;"
-                               " HBM peak of measured (MEASURED_PEAKS.json)"}
+                "kernel": "FP64-accurate fused apply in double-word arithmetic on the FP32 pipe"
+                          " (element-matrix body p=1,2, line body p>=3), all orders",
+                "peak_source": "HBM copy bandwidth of measured (MEASURED_PEAKS.json)"}
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

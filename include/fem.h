@@ -131,6 +131,24 @@ fem_status fem_mesh_create_vertices(int p, int64_t N, int64_t E,
  * more than two elements, or more than 2^31-1 nodes. */
 fem_status fem_mesh_connectivity(int p, int64_t nvert, int64_t E, const int32_t *elem_verts_host,
                                  int32_t *elem_nodes_host, uint8_t *dirichlet_host, int64_t *N_out);
+/* Generator of the bake-off meshes (section "Benchmarks": the BPs on brick
+ * meshes of the unit cube): nx*ny*nz trilinear bricks of [0,1]^3 with Q_p
+ * nodes, built on the host and uploaded like fem_mesh_create_vertices.
+ *  - vertex (i,j,k) = i + (nx+1)(j + (ny+1)k) sits at (i/nx, j/ny, k/nz); each
+ *    coordinate d of a vertex not on a face normal to d is moved by
+ *    perturb * h_d * (2u - 1), u = (SplitMix64 output 3v + d of `seed`) >> 11
+ *    times 2^-53 (Steele, Lea & Flood 2014), h_d the element size along d;
+ *    coordinates on the cube's faces stay, so the domain is exactly [0,1]^3;
+ *  - element (ex,ey,ez) = ex + nx(ey + ny ez), its local vertex t at offset
+ *    (t & 1, t >> 1 & 1, t >> 2 & 1);
+ *  - node (I,J,K) = I + Mx(J + My K), Mx = p nx + 1 (likewise My, Mz); local
+ *    node (a,b,c) of element (ex,ey,ez) is (p ex + a, p ey + b, p ez + c);
+ *  - Dirichlet marker 1 on every node of the cube's surface.
+ * With perturb = 0 the mesh is the Cartesian one.  FEM_EINVAL for p outside
+ * [1, 8], a size < 1, perturb outside [0, 0.5) or more than 2^31-1 nodes.
+ * The mesh (nodes, connectivity) is the caller's to destroy. */
+fem_status fem_mesh_box(int p, int nx, int ny, int nz, double perturb, uint64_t seed,
+                        void *stream, fem_mesh **out);
 /* Node coordinates [N][3] of a mesh, copied to host (synchronizes). */
 fem_status fem_mesh_node_coords(const fem_mesh *mesh, double *xyz_host);
 fem_status fem_mesh_destroy(fem_mesh *mesh);
@@ -205,10 +223,20 @@ fem_status fem_op_rhs(fem_op *op, int which, double *b);
  * only), 7 = the element-matrix body (one thread per element with the
  * operator's assembled element matrices; diffusion with a non-collocated
  * rule at p = 1 and 2 only).  The collocated mass operator (pointwise) has
- * choice 0 only.  blocks_per_sm: resident blocks per SM (0 = the occupancy
+ * choice 0 only.  FP64 only, the double-word bodies: every product and sum
+ * in double-word arithmetic (pairs of FP32 numbers, ~48 bits) on the FP32
+ * pipe, with FP64 vectors and FP64 atomic scatter: 8, 9, 10 = the line-based
+ * body with the three sizes, 11 = the element-matrix body (where 7 exists),
+ * 12, 13, 14 = 8, 9, 10 with the next element group's x gather carried one
+ * group ahead (scalar whole-mesh launches; otherwise as 8, 9, 10).  Their
+ * error against exact FP64 arithmetic: ~5e-14 relative l2 for random x; for
+ * diffusion each element's x_e is shifted by its node-0 value first (A_e
+ * annihilates constants), which keeps the smoothest fields within ~1e-12 at
+ * 8e6 DOFs; x values below 2^-74 in magnitude lose the low word (FP32's
+ * exponent range).  blocks_per_sm: resident blocks per SM (0 = the occupancy
  * maximum).  Defaults: the fastest choice of a sweep at 8e6 DOFs per order
- * and operator type; among them 7 for Gauss diffusion at p = 1 (FP64 and
- * FP32) and p = 2 (FP64). */
+ * and operator type; FP64: the double-word bodies; FP32: 7 for Gauss
+ * diffusion at p = 1, the line body elsewhere. */
 typedef struct {
   int epb_choice;
   int blocks_per_sm;
@@ -273,6 +301,32 @@ typedef struct {
 fem_status fem_cg_solve(fem_op *op, const double *b, double *x,
                         const fem_cg_opts *opts, fem_cg_stats *stats);
 
+/* Checkpoint and resume of a CG solve (fem_cg_solve) that stopped at its
+ * iteration cap (status FEM_ENOCONV, or maxit reached with rtol = 0).  The
+ * operator keeps that solve's state: r_k, z_k = M^-1 r_k, the previous
+ * direction and the scalars (r^T z, beta, ||b||^2, iterations); x_k is the
+ * caller's vector.
+ *  fem_cg_checkpoint_size: bytes of the state (a header, the scalars, three
+ *    ncomp*N FP64 vectors).
+ *  fem_cg_checkpoint: copy the state to host memory of that size
+ *    (synchronizes).  FEM_EINVAL if the operator has run no CG solve.
+ *  fem_cg_restore: load a state into an operator of the same size (another
+ *    process, or after the solve's workspace was reused); allocates the CG
+ *    workspace if needed.  FEM_EINVAL for a buffer that is no checkpoint of
+ *    that size.
+ *  fem_cg_resume: continue from the state with x = x_k (device [ncomp*N])
+ *    for at most opts->maxit further iterations to opts->rtol (relative to
+ *    the original ||b||); opts->precond must be the interrupted solve's.  The
+ *    iterates are those of the uninterrupted solve up to the order of the
+ *    apply's atomic additions; stats->iterations counts from the original
+ *    start.  Host-driven launches (no CUDA graph); synchronizes.  FEM_EINVAL
+ *    when the last solve did not stop at its cap. */
+fem_status fem_cg_checkpoint_size(const fem_op *op, int64_t *bytes);
+fem_status fem_cg_checkpoint(fem_op *op, void *state_host);
+fem_status fem_cg_restore(fem_op *op, const void *state_host);
+fem_status fem_cg_resume(fem_op *op, const double *b, double *x,
+                         const fem_cg_opts *opts, fem_cg_stats *stats);
+
 /* Mixed-precision solve of the same constrained system: FP64 iterative
  * refinement (classical; the paper fixes only the operator and CG) around an
  * inner Jacobi-PCG (or plain CG) that runs the FP32 apply on FP32 vectors
@@ -309,6 +363,14 @@ fem_status fem_mlp_create(int n_in, int n_h, int n_out, int mode,
 fem_status fem_mlp_destroy(fem_mlp *mlp);
 /* Current parameters to host (params_host may be NULL) and their count. */
 fem_status fem_mlp_params(fem_mlp *mlp, float *params_host, int64_t *count);
+/* Save the network's state to a file: sizes, mode, the Adam step count,
+ * the FP32 parameters and both Adam moment arrays (the format is the
+ * library's own: an 8-byte tag, six int32, int64 count, 3 * count FP32).
+ * fem_mlp_load creates a network from such a file on `stream`; training
+ * continues from the saved step as if it had not stopped.  FEM_EINVAL when
+ * the file cannot be opened or is not a saved network. */
+fem_status fem_mlp_save(fem_mlp *mlp, const char *path);
+fem_status fem_mlp_load(const char *path, void *stream, fem_mlp **out);
 /* Y [rows][n_out] FP32 = network(X). */
 fem_status fem_mlp_forward(fem_mlp *mlp, const void *X, int64_t rows, float *Y);
 /* One Adam step (lr; b1 = 0.9, b2 = 0.999, eps = 1e-8) on the loss

@@ -82,6 +82,8 @@ def lib():
         "fem_mesh_create_vertices": [ctypes.c_int, _I64, _I64, _VP, _I64, _VP, _VP, _VP, _VP,
                                      ctypes.POINTER(_VP)],
         "fem_mesh_node_coords": [_VP, _VP],
+        "fem_mesh_box": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                         ctypes.c_uint64, _VP, ctypes.POINTER(_VP)],
         "fem_mesh_connectivity": [ctypes.c_int, _I64, _I64, _VP, _VP, _VP,
                                   ctypes.POINTER(ctypes.c_int64)],
         "fem_op_create": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -96,12 +98,18 @@ def lib():
         "fem_op_rhs": [_VP, ctypes.c_int, _VP],
         "fem_cg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_solve_refined": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
+        "fem_cg_checkpoint_size": [_VP, ctypes.POINTER(ctypes.c_int64)],
+        "fem_cg_checkpoint": [_VP, _VP],
+        "fem_cg_restore": [_VP, _VP],
+        "fem_cg_resume": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_op_set_launch_shape": [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int],
         "fem_op_autotune": [_VP, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(_TuneResult)],
         "fem_op_residual": [_VP, _VP, _VP, _VP],
         "fem_mlp_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                            ctypes.POINTER(_VP)],
         "fem_mlp_destroy": [_VP],
+        "fem_mlp_save": [_VP, ctypes.c_char_p],
+        "fem_mlp_load": [ctypes.c_char_p, _VP, ctypes.POINTER(_VP)],
         "fem_mlp_params": [_VP, _VP, ctypes.POINTER(ctypes.c_int64)],
         "fem_mlp_forward": [_VP, _VP, _I64, _VP],
         "fem_mlp_train_step": [_VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_float, _VP,
@@ -260,6 +268,25 @@ class Mesh:
                                          _ptr(dr), _stream_handle(stream), ctypes.byref(h)))
         self._h = h
 
+    @classmethod
+    def box(cls, p, nx, ny=None, nz=None, perturb=0.1, seed=0, stream=None):
+        """The library's bake-off mesh generator (fem_mesh_box): nx*ny*nz
+        perturbed bricks of the unit cube with Q_p nodes, built and uploaded
+        by the library."""
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        h = _VP()
+        _check(lib().fem_mesh_box(int(p), int(nx), int(ny), int(nz), float(perturb), int(seed),
+                                  _stream_handle(stream), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.p = int(p)
+        self.E = int(nx) * int(ny) * int(nz)
+        self.N = (p * nx + 1) * (p * ny + 1) * (p * nz + 1)
+        self.dirichlet = None
+        self._xyz = None
+        self._h = h
+        return self
+
     @property
     def node_xyz(self):
         """Node coordinates [N, 3] (copied from the device on first use)."""
@@ -366,6 +393,31 @@ class Operator:
         import torch
         rc = lib().fem_cg_solve(self._h, _vec(b, torch.float64, self.n, "b"),
                                 _vec(x, torch.float64, self.n, "x"), ctypes.byref(o), ctypes.byref(st))
+        if rc not in (0, 5):
+            _check(rc)
+        return _stats(st)
+
+    def cg_checkpoint(self):
+        """The state of this operator's last CG solve (fem_cg_checkpoint) as
+        a host byte array."""
+        n = ctypes.c_int64()
+        _check(lib().fem_cg_checkpoint_size(self._h, ctypes.byref(n)))
+        buf = np.zeros(n.value, dtype=np.uint8)
+        _check(lib().fem_cg_checkpoint(self._h, _ptr(buf)))
+        return buf
+
+    def cg_restore(self, state):
+        """Load a state from cg_checkpoint (fem_cg_restore)."""
+        buf = np.ascontiguousarray(state, dtype=np.uint8)
+        _check(lib().fem_cg_restore(self._h, _ptr(buf)))
+
+    def cg_resume(self, b, x, precond=PC_JACOBI, maxit=10000, rtol=1e-10):
+        """Continue an interrupted solve from x (fem_cg_resume)."""
+        import torch
+        o = _CgOpts(precond, int(maxit), float(rtol), 0, 0.0, 0, 0)
+        st = _CgStats()
+        rc = lib().fem_cg_resume(self._h, _vec(b, torch.float64, self.n, "b"),
+                                 _vec(x, torch.float64, self.n, "x"), ctypes.byref(o), ctypes.byref(st))
         if rc not in (0, 5):
             _check(rc)
         return _stats(st)
@@ -498,6 +550,23 @@ class Mlp:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.fem_mlp_destroy(self._h)
             self._h = None
+
+    def save(self, path):
+        """Parameters, Adam moments and step count to a file (fem_mlp_save)."""
+        _check(lib().fem_mlp_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """A network restored from fem_mlp_save's file (fem_mlp_load)."""
+        import struct
+        h = _VP()
+        _check(lib().fem_mlp_load(os.fsencode(path), _stream_handle(stream), ctypes.byref(h)))
+        with open(path, "rb") as f:
+            n_in, n_h, n_out, mode = struct.unpack("<4i", f.read(24)[8:24])
+        self = cls.__new__(cls)
+        self.n_in, self.n_h, self.n_out, self.mode = n_in, n_h, n_out, mode
+        self._h = h
+        return self
 
     @property
     def input_dtype(self):

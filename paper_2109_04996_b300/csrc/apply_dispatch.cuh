@@ -72,8 +72,10 @@ int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   return FEM_OK;
 }
 
+// pipe: carry the next group's x gather one group ahead (double words; the
+// FP32 body always does for scalar whole-mesh launches)
 template <typename T, int P, int Q, bool COLLOC, int EPB, int KIND>
-int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
+int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps, bool pipe = false) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
   if constexpr (NT > 1024 || smem > 200 * 1024) {
@@ -91,8 +93,8 @@ int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps) {
     make_symtab<T, Q, P>(Bt, lp.t.Bt);
     make_symtab<T, Q, Q>(op->tab.Dq, lp.t.Df);
     make_symtab<T, Q, Q>(Dt, lp.t.Dt);
-    if constexpr (sizeof(T) == 4) {
-      if (prm.ncomp == 1 && !prm.list)
+    if constexpr (sizeof(T) == 4 || std::is_same<T, dw>::value) {
+      if (prm.ncomp == 1 && !prm.list && (sizeof(T) == 4 || pipe))
         return launch_lines_kernel<T, P, Q, COLLOC, EPB, true, KIND>(op, lp, bps);
     }
     return launch_lines_kernel<T, P, Q, COLLOC, EPB, false, KIND>(op, lp, bps);
@@ -142,7 +144,8 @@ int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
   ElmatParams<T> ep;
   ep.a = prm;
   ep.E = op->E;
-  if constexpr (sizeof(T) == 8) ep.K = reinterpret_cast<const T *>(op->d_kel);
+  if constexpr (std::is_same<T, dw>::value) ep.K = op->d_keldw;
+  else if constexpr (sizeof(T) == 8) ep.K = reinterpret_cast<const T *>(op->d_kel);
   else ep.K = reinterpret_cast<const T *>(op->d_kel32);
   if (!ep.K) {
     fem_set_error("apply: the element-matrix body needs the operator's element matrices");
@@ -173,8 +176,33 @@ int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
 // p = 1 only; the slab body's default elsewhere), 7 the element-matrix body
 // (Gauss diffusion at p = 1, 2); the collocated mass operator (pointwise)
 // has only the slab body.
+// Double words (FP64 operators, choices 8..11): the line body and the
+// element-matrix body.
+template <int P, int Q, int KIND, bool COLLOC>
+int launch_epb_dw(fem_op *op, const ApplyParams<dw> &prm, int choice, int bps) {
+  if constexpr ((P == 2 || P == 3) && KIND == FEM_DIFFUSION && !COLLOC) {
+    if (choice == FEM_CHOICE_DW_ELMAT) return launch_elmat<dw, P>(op, prm, bps);
+  }
+  if constexpr (KIND == FEM_DIFFUSION || !COLLOC) {
+    switch (choice) {
+      case 8: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps);
+      case 9: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps);
+      case 10: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps);
+      case 12: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps, true);
+      case 13: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps, true);
+      case 14: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps, true);
+      default: break;
+    }
+  }
+  fem_set_error("apply: launch choice %d has no double-word body for this operator", choice);
+  return FEM_EINVAL;
+}
+
 template <typename T, int P, int Q, int KIND, bool COLLOC>
 int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
+  if constexpr (std::is_same<T, dw>::value) {
+    return launch_epb_dw<P, Q, KIND, COLLOC>(op, prm, choice, bps);
+  } else {
   if constexpr (P == 2 && KIND == FEM_DIFFUSION && !COLLOC) {
     if (choice == 6) return launch_trilinear<T, Q>(op, prm, bps);
   }
@@ -196,6 +224,7 @@ int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
     case 2: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 2>::value>(op, prm, bps);
     default: return launch_shape<T, P, Q, KIND, COLLOC, EpbChoice<Q, 0>::value>(op, prm, bps);
   }
+  }
 }
 
 // Launch shapes are tunable (epb_choices) except for the collocated mass
@@ -205,9 +234,15 @@ int dispatch_q(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
   constexpr int QG = (P + 1 <= FEM_MAX_Q) ? P + 1 : P;
   const bool diff = op->kind == FEM_DIFFUSION;
   if (op->Q == P) {
-    if (op->colloc)
-      return diff ? launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps)
-                  : launch_shape<T, P, P, FEM_MASS, true, EpbChoice<P, 0>::value>(op, prm, bps);
+    if (op->colloc) {
+      if (diff) return launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps);
+      if constexpr (std::is_same<T, dw>::value) {
+        fem_set_error("apply: the collocated mass operator has no double-word body");
+        return FEM_EINVAL;
+      } else {
+        return launch_shape<T, P, P, FEM_MASS, true, EpbChoice<P, 0>::value>(op, prm, bps);
+      }
+    }
     return diff ? launch_epb<T, P, P, FEM_DIFFUSION, false>(op, prm, choice, bps)
                 : launch_epb<T, P, P, FEM_MASS, false>(op, prm, choice, bps);
   }

@@ -25,9 +25,18 @@ namespace fem_apply {
 template <typename T>
 struct ElmatParams {
   ApplyParams<T> a;
-  const T *K;     // [P^3 (P^3 + 1) / 2][E]
+  const T *K;     // [P^3 (P^3 + 1) / 2][E] (double words: split FP64 K_e)
   int64_t E;      // element stride of K (all elements of the operator)
 };
+
+// One K_e entry, streamed once per apply (evict-first).
+template <typename T>
+__device__ __forceinline__ T ld_entry(const T *p) { return __ldcs(p); }
+template <>
+__device__ __forceinline__ dw ld_entry<dw>(const dw *p) {
+  const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+  return dw(v.x, v.y);
+}
 
 constexpr int kElmatThreads = 128;
 
@@ -36,17 +45,29 @@ template <typename T, int P>
 __device__ __forceinline__ void elmat_element(const ApplyParams<T> &prm, const T *__restrict__ K,
                                               int64_t E, int64_t e, DotAcc<T> &dl) {
   constexpr int P3 = P * P * P;
-  int id[P3];
+  // at P = 3 double words hold x_e and y_e in 108 registers: the node ids
+  // are read again for the scatter (L1 hits) instead of being kept
+  constexpr bool KEEP_IDS = !std::is_same<T, dw>::value || P == 2;
+  int id[KEEP_IDS ? P3 : 1];
   const int32_t *en = prm.elem_nodes + e * P3;
+  if constexpr (KEEP_IDS) {
 #pragma unroll
-  for (int a = 0; a < P3; a++) id[a] = en[a];
+    for (int a = 0; a < P3; a++) id[a] = en[a];
+  }
+  auto node = [&](int a) -> int { if constexpr (KEEP_IDS) return id[a]; else return en[a]; };
   for (int c = 0; c < prm.ncomp; c++) {
-    const T *xc = prm.x + c * prm.N;
-    T *yc = prm.y + c * prm.N;
+    const auto *xc = prm.x + c * prm.N;
+    auto *yc = prm.y + c * prm.N;
     T x[P3], y[P3];
+    // double words: x_e - x_0 1 (ShiftX; K_e annihilates constants)
+    // (at P = 2 the shift's FP64 subtractions and the registers of the
+    // unshifted values cost 2x, and the smoothest fields stay within 1e-12
+    // without it: 7e-13 at 8e6 DOFs)
+    constexpr bool SH = ShiftX<T, FEM_DIFFUSION>::value && P > 2;
+    const double c0 = SH ? (double)gather_load(&xc[node(0)], prm.x_l2_only) : 0.0;
 #pragma unroll
     for (int a = 0; a < P3; a++) {
-      x[a] = gather_load(&xc[id[a]], prm.x_l2_only);
+      x[a] = gather_shifted<T, SH>(&xc[node(a)], prm.x_l2_only, c0);
       y[a] = T(0);
     }
     // the entries in their packed order: K_e is streamed once per apply
@@ -56,7 +77,7 @@ __device__ __forceinline__ void elmat_element(const ApplyParams<T> &prm, const T
     for (int a = 0; a < P3; a++) {
 #pragma unroll
       for (int b = a; b < P3; b++) {
-        const T kv = __ldcs(kp);
+        const T kv = ld_entry(kp);
         kp += E;
         y[a] = fma(kv, x[b], y[a]);
         if (b != a) y[b] = fma(kv, x[a], y[b]);
@@ -64,7 +85,7 @@ __device__ __forceinline__ void elmat_element(const ApplyParams<T> &prm, const T
     }
 #pragma unroll
     for (int a = 0; a < P3; a++) {
-      atomic_add(&yc[id[a]], y[a]);
+      atomic_add(&yc[node(a)], y[a]);
       dl.add(y[a], x[a]);
     }
   }

@@ -4,6 +4,8 @@
 int fem_launch_apply_f64_shape(fem_op *op, const double *x, double *y, const int32_t *list,
                                int64_t nsel, double *dot_out, int choice, int bps,
                                const int *skip) {
+  if (fem_choice_is_dw(choice))
+    return fem_launch_apply_dw_shape(op, x, y, list, nsel, dot_out, choice, bps, skip);
   fem_apply::ApplyParams<double> prm;
   prm.x = x; prm.y = y;
   prm.elem_nodes = op->mesh->d_elem_nodes;

@@ -20,22 +20,52 @@
 // loop over element groups.  Gauss-Lobatto with q = p+1 (BP5/BP6) skips the
 // interpolation (identity).
 #pragma once
+#include <type_traits>
+
+#include "dw.cuh"
 #include "fem_internal.h"
 
 namespace fem_apply {
 
+// Storage of the vectors and of the pointwise data for arithmetic type T:
+// T itself for FP64 and FP32; the double-word bodies (T = dw) read and
+// write the FP64 vectors, splitting each gathered x value into a double word
+// by integer operations and rounding each element result back to FP64, and
+// read the operator's double-word copy of the qdata (split once at set-up:
+// FP64 <-> FP32 conversions run at the FP64 rate).
+template <typename T>
+struct Store {
+  using V = T;   // x, y
+  using Q = T;   // qdata, tables
+};
+template <>
+struct Store<dw> {
+  using V = double;
+  using Q = dw;
+};
+
+// Value of a stored entry in arithmetic type T.
+template <typename T, typename S>
+__device__ __forceinline__ T to_arith(S v) {
+  if constexpr (std::is_same<T, dw>::value && std::is_same<S, double>::value)
+    return dw_from_double_int(v);
+  else return v;
+}
+
 template <typename T>
 struct ApplyParams {
-  const T *x;
-  T *y;
+  using V = typename Store<T>::V;
+  using QS = typename Store<T>::Q;
+  const V *x;
+  V *y;
   const int32_t *elem_nodes;  // [E][P^3]
   const int32_t *list;        // optional element list
   int64_t nsel;               // number of elements to process
   int64_t N;
   int ncomp;
-  const T *qdata;             // [E][nd][Q^3]
-  const T *B;                 // [Q][P]
-  const T *Dq;                // [Q][Q]
+  const QS *qdata;            // [E][nd][Q^3]
+  const QS *B;                // [Q][P]
+  const QS *Dq;               // [Q][Q]
   double *partials;           // fused x.y (optional)
   unsigned *counter;
   double *dot_out;
@@ -81,9 +111,43 @@ struct DotAcc<float> {
   __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
+// Double word: TwoSum accumulation of the exact double-word products.
+template <>
+struct DotAcc<dw> {
+  dw v = dw(0.0f, 0.0f);
+  __device__ __forceinline__ void add(dw a, dw b) { v += a * b; }
+  __device__ __forceinline__ double get() const { return dw_to_double(v); }
+};
+
 template <typename T>
 __device__ __forceinline__ T gather_load(const T *p, int l2_only) {
   return l2_only ? __ldcg(p) : *p;
+}
+
+// x entry in arithmetic type T (the double-word bodies split the FP64 value).
+template <typename T, typename S>
+__device__ __forceinline__ T gather_arith(const S *p, int l2_only) {
+  return to_arith<T>(gather_load(p, l2_only));
+}
+
+// The double-word diffusion bodies apply A_e to x_e - c 1 (c = x at the
+// element's local node 0) instead of x_e: A_e annihilates constants, so the
+// result and the element's x_e^T A_e x_e are unchanged, but the values that
+// enter the double-word contractions are differences of nearby nodal values
+// (the FP64 subtraction is exact for close values, Sterbenz 1974) rather
+// than the values themselves.  The ~2^-47 relative noise of double-word
+// arithmetic then scales with h |grad x| instead of |x|, which keeps smooth
+// inputs -- whose gradients are interpolated from nearly equal values --
+// within FP64-level accuracy.
+template <typename T, int KIND>
+struct ShiftX {
+  static constexpr bool value = std::is_same<T, dw>::value && KIND == FEM_DIFFUSION;
+};
+
+template <typename T, bool SH, typename S>
+__device__ __forceinline__ T gather_shifted(const S *p, int l2_only, double c) {
+  if constexpr (SH) return to_arith<T>((double)gather_load(p, l2_only) - c);
+  else return gather_arith<T>(p, l2_only);
 }
 
 // Elements per block of the default shape: about 256 threads.
@@ -144,6 +208,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <typename T>
 __device__ __forceinline__ void atomic_add(T *a, T v) { atomicAdd(a, v); }
+__device__ __forceinline__ void atomic_add(double *a, dw v) { atomicAdd(a, dw_to_double_int(v)); }
 
 // Thread-local view of one block: slot, slab coordinates and shared buffers.
 template <typename T, int P, int Q, int KIND, int EPB>

@@ -70,6 +70,47 @@ __device__ __forceinline__ void sym_apply(const SymTab<T, NI, NO> &M, const T (&
   }
 }
 
+// Double words: every output starts from its first product rather than a
+// TwoSum with zero (the generic form above spends 6 instructions on that).
+template <int S, int NI, int NO>
+__device__ __forceinline__ void sym_apply(const SymTab<dw, NI, NO> &M, const dw (&in)[NI],
+                                          dw (&out)[NO]) {
+  constexpr int HI = NI / 2, HO = NO / 2;
+  static_assert(HI > 0, "lines have at least two entries");
+  dw ie[HI], io[HI];
+#pragma unroll
+  for (int a = 0; a < HI; a++) {
+    ie[a] = in[a] + in[NI - 1 - a];
+    io[a] = in[a] - in[NI - 1 - a];
+  }
+#pragma unroll
+  for (int k = 0; k < HO; k++) {
+    dw A = M.e[k][0] * ie[0], Bv = M.o[k][0] * io[0];
+#pragma unroll
+    for (int a = 1; a < HI; a++) {
+      A += M.e[k][a] * ie[a];
+      Bv += M.o[k][a] * io[a];
+    }
+    if constexpr (NI % 2 == 1) A += M.mid[k] * in[HI];
+    out[k] = A + Bv;
+    out[NO - 1 - k] = (S > 0) ? A - Bv : Bv - A;
+  }
+  if constexpr (NO % 2 == 1) {
+    if constexpr (S > 0) {
+      dw v = M.e[HO][0] * ie[0];
+#pragma unroll
+      for (int a = 1; a < HI; a++) v += M.e[HO][a] * ie[a];
+      if constexpr (NI % 2 == 1) v += M.mid[HO] * in[HI];
+      out[HO] = v;
+    } else {
+      dw v = M.o[HO][0] * io[0];
+#pragma unroll
+      for (int a = 1; a < HI; a++) v += M.o[HO][a] * io[a];
+      out[HO] = v;
+    }
+  }
+}
+
 template <typename T, int P, int Q>
 struct LineTables {
   static constexpr int kP = P, kQ = Q;
@@ -85,6 +126,14 @@ struct LineParams {
   LineTables<T, P, Q> t;
 };
 
+// Host: a table entry in arithmetic type T (double words split the FP64
+// value, h = fl32(v), l = fl32(v - h)).
+template <typename T>
+inline T tab_value(double v) {
+  if constexpr (std::is_same<T, dw>::value) return dw_split_host(v);
+  else return (T)v;
+}
+
 // Host: split a row-major M[NO][NI] (FP64) into the table.
 template <typename T, int NI, int NO>
 inline void make_symtab(const double *M, SymTab<T, NI, NO> &s) {
@@ -92,14 +141,14 @@ inline void make_symtab(const double *M, SymTab<T, NI, NO> &s) {
   for (int k = 0; k <= HO && k < NO; k++) {
     for (int a = 0; a < (HI > 0 ? HI : 1); a++) {
       if (a < HI) {
-        s.e[k][a] = (T)(0.5 * (M[k * NI + a] + M[k * NI + NI - 1 - a]));
-        s.o[k][a] = (T)(0.5 * (M[k * NI + a] - M[k * NI + NI - 1 - a]));
+        s.e[k][a] = tab_value<T>(0.5 * (M[k * NI + a] + M[k * NI + NI - 1 - a]));
+        s.o[k][a] = tab_value<T>(0.5 * (M[k * NI + a] - M[k * NI + NI - 1 - a]));
       } else {
-        s.e[k][a] = (T)0;
-        s.o[k][a] = (T)0;
+        s.e[k][a] = tab_value<T>(0.0);
+        s.o[k][a] = tab_value<T>(0.0);
       }
     }
-    s.mid[k] = (NI % 2 == 1) ? (T)M[k * NI + HI] : (T)0;
+    s.mid[k] = tab_value<T>((NI % 2 == 1) ? M[k * NI + HI] : 0.0);
   }
 }
 
@@ -150,6 +199,7 @@ template <typename T, int P>
 struct Column {
   int32_t idx[P];
   T u[P];
+  int32_t idx0;   // the element's local node 0 (shifted double-word bodies)
 };
 
 // Column of element group g for the calling thread (a P x P line set
@@ -163,13 +213,16 @@ __device__ __forceinline__ void column_indices(const ApplyParams<T> &prm, int64_
   const int32_t *en = prm.elem_nodes + (ok ? k_el : 0) * P3 + (t % P) + P * (t / P);
 #pragma unroll
   for (int k = 0; k < P; k++) col.idx[k] = ok ? en[P2 * k] : -1;
+  col.idx0 = ok ? prm.elem_nodes[k_el * P3] : -1;
 }
 
-template <typename T, int P>
+// SH: values shifted by x at the element's node 0 (ShiftX).
+template <typename T, int P, bool SH = false>
 __device__ __forceinline__ void column_values(const ApplyParams<T> &prm, Column<T, P> &col) {
+  const double c0 = (SH && col.idx0 >= 0) ? (double)gather_load(&prm.x[col.idx0], prm.x_l2_only) : 0.0;
 #pragma unroll
   for (int k = 0; k < P; k++)
-    col.u[k] = col.idx[k] >= 0 ? gather_load(&prm.x[col.idx[k]], prm.x_l2_only) : T(0);
+    col.u[k] = col.idx[k] >= 0 ? gather_shifted<T, SH>(&prm.x[col.idx[k]], prm.x_l2_only, c0) : T(0);
 }
 
 // PIPE (scalar operator, contiguous elements): the column of this group is
@@ -186,6 +239,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
                                                   const Column<T, P> *cur = nullptr,
                                                   Column<T, P> *nxt = nullptr) {
   constexpr bool DIFF = KIND == FEM_DIFFUSION;
+  constexpr bool SH = ShiftX<T, KIND>::value;
   static_assert(DIFF || !COLLOC, "the collocated mass operator is pointwise: slab body");
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P2 = P * P, P3 = P * P * P;
   using Cube = LineCube<Q, PAD, (int)sizeof(T)>;
@@ -201,7 +255,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   int64_t e = 0;
   if (valid) e = prm.list ? (int64_t)prm.list[k_el] : k_el;
   const int32_t *en = prm.elem_nodes + e * P3;
-  const T *qd = prm.qdata + e * (int64_t)((DIFF ? 6 : 1) * Q3);
+  const auto *qd = prm.qdata + e * (int64_t)((DIFF ? 6 : 1) * Q3);
   // line coordinates of this thread: (t % Q, t / Q) for q-by-q line sets,
   // (t % P, t / P) for P-by-q, (t % P, t / P) for P-by-P
   const int lq0 = t % Q, lq1 = t / Q;
@@ -214,17 +268,19 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   DotAcc<T> dl;
   if constexpr (PIPE) column_indices<T, P, Q, EPB>(prm, g + gridDim.x, *nxt);
   for (int c = 0; c < prm.ncomp; c++) {
-    const T *xc = prm.x + c * N;
-    T *yc = prm.y + c * N;
+    const auto *xc = prm.x + c * N;
+    auto *yc = prm.y + c * N;
     // ---- gather the z-column (a, b) = (lp0, lp1) of the element
     T u[P];
     if constexpr (PIPE) {
 #pragma unroll
       for (int k = 0; k < P; k++) u[k] = cur->u[k];
     } else {
+      const double c0 = (SH && valid) ? (double)gather_load(&xc[en[0]], prm.x_l2_only) : 0.0;
 #pragma unroll
       for (int k = 0; k < P; k++)
-        u[k] = (valid && on_pp) ? gather_load(&xc[en[lp0 + P * lp1 + P2 * k]], prm.x_l2_only) : T(0);
+        u[k] = (valid && on_pp) ? gather_shifted<T, SH>(&xc[en[lp0 + P * lp1 + P2 * k]], prm.x_l2_only, c0)
+                                : T(0);
     }
     // c3 holds the values at the quadrature points, x-contiguous [k][j][i]
     if constexpr (COLLOC) {
@@ -263,13 +319,13 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
     }
     __syncthreads();
     if constexpr (!DIFF) {
-      if constexpr (PIPE) column_values<T, P>(prm, *nxt);
+      if constexpr (PIPE) column_values<T, P, SH>(prm, *nxt);
       // ---- mass: values at the quadrature points times w detJ, in place
       if (on_qq) {
 #pragma unroll
         for (int kq = 0; kq < Q; kq++) {
           const int pt = cube_ix<SJ, SK>(kq, lq1, lq0);
-          const T w = valid ? qd[(kq * Q + lq1) * Q + lq0] : T(0);
+          const T w = valid ? to_arith<T>(qd[(kq * Q + lq1) * Q + lq0]) : T(0);
           c3[pt] *= w;
         }
       }
@@ -298,7 +354,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       for (int m = 0; m < Q; m++) c4[cube_ix<SJ, SK>(m, lq1, lq0)] = out[m];
     }
     __syncthreads();
-    if constexpr (PIPE) column_values<T, P>(prm, *nxt);
+    if constexpr (PIPE) column_values<T, P, SH>(prm, *nxt);
     // ---- pointwise D at the column (iq, jq) = (lq0, lq1), in place
     if (on_qq) {
 #pragma unroll
@@ -307,9 +363,9 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T G00 = 0, G11 = 0, G22 = 0, G12 = 0, G02 = 0, G01 = 0;
         if (valid) {
           // qdata is unpadded: the cube index unless the cube is padded
-          const T *qk = qd + ((SJ == Q && SK == Q * Q) ? pt : (kq * Q + lq1) * Q + lq0);
-          G00 = qk[0]; G11 = qk[Q3]; G22 = qk[2 * Q3];
-          G12 = qk[3 * Q3]; G02 = qk[4 * Q3]; G01 = qk[5 * Q3];
+          const auto *qk = qd + ((SJ == Q && SK == Q * Q) ? pt : (kq * Q + lq1) * Q + lq0);
+          G00 = to_arith<T>(qk[0]); G11 = to_arith<T>(qk[Q3]); G22 = to_arith<T>(qk[2 * Q3]);
+          G12 = to_arith<T>(qk[3 * Q3]); G02 = to_arith<T>(qk[4 * Q3]); G01 = to_arith<T>(qk[5 * Q3]);
         }
         const T gx = c1[pt], gy = c2[pt], gz = c4[pt];
         c1[pt] = G00 * gx + G01 * gy + G02 * gz;
@@ -418,7 +474,7 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
   if constexpr (PIPE) {
     Column<T, P> cur, nxt;
     column_indices<T, P, Q, EPB>(prm, blockIdx.x, cur);
-    column_values<T, P>(prm, cur);
+    column_values<T, P, ShiftX<T, KIND>::value>(prm, cur);
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
       apply_group_lines<T, P, Q, COLLOC, EPB, true, true, KIND>(prm, lp.t, g, cubes, dot, &cur, &nxt);
       cur = nxt;

@@ -781,6 +781,8 @@ static int create_persistent(fem_op *const *ops, int n, fem_batch **out) {
   BatchLineTables htab;   // host image of the constant tables (uploaded per slot)
   bool have_tab[FEM_MAX_P + 1] = {};
   for (int i = 0; ok && i < n; i++) {
+    // the batch's FP64 residual kernel reads the FP64 qdata
+    if (fem_ensure_qdata64(ops[i]) != FEM_OK) { ok = false; break; }
     const fem_op *op = ops[i];
     BatchProblem &p = b->h_prob[i];
     p.P = op->P; p.Q = op->Q; p.ncomp = op->ncomp; p.N = op->N; p.E = op->E;

@@ -104,8 +104,13 @@ __global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n);
 
 // The trilinear body's line sums (fem_op::d_qsum), made when that body is
 // first selected: the trilinear body applies the diagonal of D once per line.
+int ensure_qdata64(fem_op *op);
 int ensure_qsum(fem_op *op) {
   if (op->d_qsum || !(op->kind == FEM_DIFFUSION && !op->colloc && op->P == 2)) return FEM_OK;
+  {
+    const int rc0 = ensure_qdata64(op);
+    if (rc0) return rc0;
+  }
   const int Q = op->Q;
   const size_t ns = (size_t)op->E * 3 * Q * Q;
   cudaStream_t s = op->stream();
@@ -120,15 +125,102 @@ int ensure_qsum(fem_op *op) {
   return FEM_OK;
 }
 
+template <typename T>
+void dev_release(T **p, size_t count, int64_t *bytes) {
+  if (!*p) return;
+  cudaFree(*p);
+  *p = nullptr;
+  *bytes -= (int64_t)(sizeof(T) * (count == 0 ? 1 : count));
+}
+
+size_t nq64(const fem_op *op) {
+  return (size_t)op->E * (op->kind == FEM_DIFFUSION ? 6 : 1) * op->Q * op->Q * op->Q;
+}
+size_t nkel(const fem_op *op) {
+  const size_t P3 = (size_t)op->P * op->P * op->P;
+  return (size_t)op->E * (P3 * (P3 + 1) / 2);
+}
+
 __global__ void f64_to_f32_kernel(const double *a, float *b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
 
+__global__ void f64_to_dw_kernel(const double *a, dw *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = dw_from_double(a[i]);
+}
+
+// The FP64 qdata, recomputed from the mesh when it was released.
+int ensure_qdata64(fem_op *op) {
+  if (op->d_qdata) return FEM_OK;
+  int rc;
+  if ((rc = dev_alloc(&op->d_qdata, nq64(op), &op->bytes))) return rc;
+  return fem_setup_qdata(op);
+}
+
+// The FP64 element matrices (Gauss diffusion at P = 2, 3), built from the
+// qdata: K_e = sum_q grad phi_a^T D grad phi_b.
+int ensure_kel64(fem_op *op) {
+  if (op->d_kel || !fem_has_elmat(op->kind, op->colloc, op->P)) return FEM_OK;
+  int rc;
+  if ((rc = ensure_qdata64(op))) return rc;
+  const size_t nk = nkel(op);
+  if ((rc = dev_alloc(&op->d_kel, nk, &op->bytes))) return rc;
+  ElmatTabs et;
+  memset(&et, 0, sizeof(et));
+  memcpy(et.B, op->tab.B, sizeof(double) * op->Q * op->P);
+  memcpy(et.G, op->tab.G, sizeof(double) * op->Q * op->P);
+  if (nk > 0) {
+    if (op->P == 2) elmat_setup_kernel<2><<<148 * 8, 128, 0, op->stream()>>>(op->d_qdata, op->E, op->Q, et, op->d_kel);
+    else elmat_setup_kernel<3><<<148 * 8, 128, 0, op->stream()>>>(op->d_qdata, op->E, op->Q, et, op->d_kel);
+    FEM_CHECK_LAUNCH();
+  }
+  return FEM_OK;
+}
+
+// The double-word split of the element matrices (choice 11), made when that
+// body is first selected.
+int ensure_keldw(fem_op *op) {
+  if (op->d_keldw || !fem_has_elmat(op->kind, op->colloc, op->P)) return FEM_OK;
+  int rc;
+  if ((rc = ensure_kel64(op))) return rc;
+  const int P3 = op->P * op->P * op->P;
+  const size_t nk = (size_t)op->E * (size_t)(P3 * (P3 + 1) / 2);
+  if ((rc = dev_alloc(&op->d_keldw, nk, &op->bytes))) return rc;
+  if (nk > 0) f64_to_dw_kernel<<<148 * 8, 256, 0, op->stream()>>>(op->d_kel, op->d_keldw, (int64_t)nk);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
 }  // namespace
 
 int fem_ensure_qsum(fem_op *op) { return ensure_qsum(op); }
+
+// The double-word split of the qdata (choices 8..10), made when one of
+// those bodies is first selected.
+static int ensure_qdw(fem_op *op) {
+  if (op->d_qdw) return FEM_OK;
+  const size_t nq = nq64(op);
+  int rc;
+  if ((rc = ensure_qdata64(op))) return rc;
+  if ((rc = dev_alloc(&op->d_qdw, nq, &op->bytes))) return rc;
+  if (nq > 0) f64_to_dw_kernel<<<148 * 8, 256, 0, op->stream()>>>(op->d_qdata, op->d_qdw, (int64_t)nq);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
+int fem_ensure_choice_data(fem_op *op, int prec, int choice) {
+  if (choice == 6) return ensure_qsum(op);
+  if (choice == FEM_CHOICE_DW_ELMAT) return ensure_keldw(op);
+  if (fem_choice_is_dw(choice)) return ensure_qdw(op);
+  if (prec == FEM_F64) return choice == 7 ? ensure_kel64(op) : ensure_qdata64(op);
+  return FEM_OK;   // the FP32 bodies read the FP32 copies made at set-up
+}
+
+int fem_ensure_qdata64(fem_op *op) { return ensure_qdata64(op); }
 
 extern "C" fem_status fem_mesh_create(int p, int64_t N, int64_t E, const int32_t *en,
                                       const double *xyz, const uint8_t *dir, void *stream,
@@ -267,6 +359,71 @@ extern "C" fem_status fem_mesh_create_vertices(int p, int64_t N, int64_t E, cons
   return FEM_OK;
 }
 
+// SplitMix64 output i of a generator whose state starts at `seed` (Steele,
+// Lea & Flood 2014): a counter-based stream.
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+extern "C" fem_status fem_mesh_box(int p, int nx, int ny, int nz, double perturb, uint64_t seed,
+                                   void *stream, fem_mesh **out) {
+  if (!out) { fem_set_error("fem_mesh_box: out is NULL"); return FEM_EINVAL; }
+  *out = nullptr;
+  if (p < 1 || p + 1 > FEM_MAX_P || nx < 1 || ny < 1 || nz < 1 || !(perturb >= 0.0 && perturb < 0.5)) {
+    fem_set_error("fem_mesh_box: need p in [1, 8], n >= 1 per direction, 0 <= perturb < 0.5");
+    return FEM_EINVAL;
+  }
+  const int P = p + 1, P3 = P * P * P;
+  const int64_t vx = nx + 1, vy = ny + 1, vz = nz + 1, nvert = vx * vy * vz;
+  const int64_t Mx = (int64_t)p * nx + 1, My = (int64_t)p * ny + 1, Mz = (int64_t)p * nz + 1;
+  const int64_t N = Mx * My * Mz, E = (int64_t)nx * ny * nz;
+  if (N > INT32_MAX || nvert > INT32_MAX) {
+    fem_set_error("fem_mesh_box: %lld nodes exceed int32 ids", (long long)N);
+    return FEM_EINVAL;
+  }
+  std::vector<double> vxyz((size_t)3 * nvert);
+  const int64_t nd[3] = {nx, ny, nz};
+  for (int64_t k = 0; k < vz; k++)
+    for (int64_t j = 0; j < vy; j++)
+      for (int64_t i = 0; i < vx; i++) {
+        const int64_t v = i + vx * (j + vy * k);
+        const int64_t idx[3] = {i, j, k};
+        for (int d = 0; d < 3; d++) {
+          const double h = 1.0 / (double)nd[d];
+          double c = (double)idx[d] * h;
+          if (idx[d] > 0 && idx[d] < nd[d] && perturb > 0.0) {
+            const double u = (double)(splitmix64_at(seed, (uint64_t)(3 * v + d)) >> 11) * 0x1.0p-53;
+            c += perturb * h * (2.0 * u - 1.0);
+          }
+          vxyz[3 * v + d] = c;
+        }
+      }
+  std::vector<int32_t> ev((size_t)8 * E), en((size_t)E * P3);
+  for (int64_t ez = 0; ez < nz; ez++)
+    for (int64_t ey = 0; ey < ny; ey++)
+      for (int64_t ex = 0; ex < nx; ex++) {
+        const int64_t e = ex + nx * (ey + ny * ez);
+        for (int t = 0; t < 8; t++)
+          ev[8 * e + t] = (int32_t)((ex + (t & 1)) + vx * ((ey + ((t >> 1) & 1)) + vy * (ez + ((t >> 2) & 1))));
+        for (int c = 0; c < P; c++)
+          for (int b = 0; b < P; b++)
+            for (int a = 0; a < P; a++)
+              en[(size_t)e * P3 + a + P * b + P * P * c] =
+                  (int32_t)((p * ex + a) + Mx * ((p * ey + b) + My * (p * ez + c)));
+      }
+  std::vector<uint8_t> dir((size_t)N);
+  for (int64_t K = 0; K < Mz; K++)
+    for (int64_t J = 0; J < My; J++)
+      for (int64_t I = 0; I < Mx; I++)
+        dir[I + Mx * (J + My * K)] =
+            (I == 0 || I == Mx - 1 || J == 0 || J == My - 1 || K == 0 || K == Mz - 1) ? 1 : 0;
+  return fem_mesh_create_vertices(p, N, E, en.data(), nvert, vxyz.data(), ev.data(), dir.data(),
+                                  stream, out);
+}
+
 extern "C" fem_status fem_mesh_node_coords(const fem_mesh *m, double *xyz_host) {
   if (!m || !xyz_host) { fem_set_error("fem_mesh_node_coords: invalid arguments"); return FEM_EINVAL; }
   std::vector<double> soa((size_t)3 * m->N);
@@ -315,17 +472,20 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   const int nd = kind == FEM_DIFFUSION ? 6 : 1;
   // Default launch shapes: the fastest choice (fem_apply_choices) of a
   // sweep of every choice at 8e6 DOFs on a B300, per P = p + 1 (index P - 2):
-  // BP3 (Gauss q = p + 2), BP5 (collocated) and BP1 (Gauss mass).  Among
-  // them: the element-matrix body (7) for Gauss diffusion at p = 1 (FP64
-  // 6.5x the trilinear body at 5e7 DOFs, FP32 3.2x) and in FP64 at p = 2
-  // (4.8x the slab body), the slab body for most collocated FP64 orders, the
-  // line body elsewhere, often with half the default elements per block (1).
+  // BP3 (Gauss q = p + 2), BP5 (collocated) and BP1 (Gauss mass).  FP32:
+  // the element-matrix body (7) for Gauss diffusion at p = 1 (3.2x the
+  // trilinear body), the line body elsewhere, often with half the default
+  // elements per block (1).  FP64: the double-word bodies everywhere (8..10
+  // line body, 12..14 with the pipelined gather, 11 element matrices at
+  // p = 1, 2): double-word arithmetic on the FP32 pipe, 3.8-4.6x the fastest
+  // FP64-arithmetic body for BP3 p = 3..7, 2.6x at p = 8, 1.4x (p = 1) and
+  // 1.07x (p = 2) over the FP64 element matrices, 2.6-4x for BP5 and BP1.
   static const int kDiffF32[8] = {7, 1, 1, 0, 1, 0, 0, 1};
-  static const int kDiffF64[8] = {7, 7, 1, 0, 0, 1, 0, 2};
+  static const int kDiffF64[8] = {11, 11, 13, 12, 12, 13, 10, 10};
   static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
-  static const int kCollF64[8] = {4, 3, 3, 4, 3, 3, 4, 2};
+  static const int kCollF64[8] = {13, 9, 12, 9, 9, 12, 13, 14};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
-  static const int kMassF64[8] = {4, 4, 1, 0, 0, 1, 1, 1};
+  static const int kMassF64[8] = {9, 13, 9, 12, 8, 9, 8, 8};
   const int ip = P - 2;   // P in 2..9
   if (kind == FEM_DIFFUSION && !op->colloc) {
     op->tune_epb[FEM_F32] = kDiffF32[ip];
@@ -380,26 +540,35 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
     if ((rc = dev_alloc(&op->d_qdata32, nq, &op->bytes))) { fem_op_destroy(op); return rc; }
     if (nq > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_qdata, op->d_qdata32, (int64_t)nq);
   }
-  if (op->tune_epb[FEM_F64] == 6 || op->tune_epb[FEM_F32] == 6) {
-    if ((rc = fem_ensure_qsum(op))) { fem_op_destroy(op); return rc; }
-  }
   if (fem_has_elmat(kind, op->colloc, P)) {
-    // element matrices for the element-matrix body (launch choice 7)
-    const int P3 = P * P * P;
-    const size_t nk = (size_t)op->E * (size_t)(P3 * (P3 + 1) / 2);
-    if ((rc = dev_alloc(&op->d_kel, nk, &op->bytes))) { fem_op_destroy(op); return rc; }
-    ElmatTabs et;
-    memset(&et, 0, sizeof(et));
-    memcpy(et.B, op->tab.B, sizeof(double) * Q * P);
-    memcpy(et.G, op->tab.G, sizeof(double) * Q * P);
-    if (nk > 0) {
-      if (P == 2) elmat_setup_kernel<2><<<148 * 8, 128, 0, s>>>(op->d_qdata, op->E, Q, et, op->d_kel);
-      else elmat_setup_kernel<3><<<148 * 8, 128, 0, s>>>(op->d_qdata, op->E, Q, et, op->d_kel);
-    }
+    // element matrices for the element-matrix bodies (launch choices 7, 11)
+    if ((rc = ensure_kel64(op))) { fem_op_destroy(op); return rc; }
     if (prec == FEM_F32) {
+      const int P3 = P * P * P;
+      const size_t nk = (size_t)op->E * (size_t)(P3 * (P3 + 1) / 2);
       if ((rc = dev_alloc(&op->d_kel32, nk, &op->bytes))) { fem_op_destroy(op); return rc; }
       if (nk > 0) f64_to_f32_kernel<<<148 * 8, 256, 0, s>>>(op->d_kel, op->d_kel32, (int64_t)nk);
     }
+  }
+  // the data of the default launch choices (trilinear line sums, split
+  // qdata or element matrices)
+  if ((rc = fem_ensure_choice_data(op, FEM_F64, op->tune_epb[FEM_F64])) ||
+      (rc = fem_ensure_choice_data(op, FEM_F32, op->tune_epb[FEM_F32]))) {
+    fem_op_destroy(op);
+    return rc;
+  }
+  // With a double-word body as the FP64 default, the FP64 qdata and element
+  // matrices are read by nothing after set-up: release them (they are
+  // rebuilt from the mesh when another body, a batch or fem_op_qdata needs
+  // them).  At 5e7 DOFs this is 65 GB at p = 1.
+  if (fem_choice_is_dw(op->tune_epb[FEM_F64])) {
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      fem_set_error("fem_op_create: setup kernels failed: %s", cudaGetErrorString(e));
+      fem_op_destroy(op);
+      return FEM_ECUDA;
+    }
+    dev_release(&op->d_qdata, nq64(op), &op->bytes);
+    if (op->d_kel) dev_release(&op->d_kel, nkel(op), &op->bytes);
   }
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -420,7 +589,7 @@ extern "C" fem_status fem_op_destroy(fem_op *op) {
   if (op->d_B32) cudaFree(op->d_B32 - TAB_B);
   cudaFree(op->d_qdata); cudaFree(op->d_qdata32); cudaFree(op->d_diag); cudaFree(op->d_rff);
   cudaFree(op->d_qsum); cudaFree(op->d_qsum32);
-  cudaFree(op->d_kel); cudaFree(op->d_kel32);
+  cudaFree(op->d_kel); cudaFree(op->d_kel32); cudaFree(op->d_keldw); cudaFree(op->d_qdw);
   cudaFree(op->d_partials); cudaFree(op->d_counter);
   delete op;
   return FEM_OK;
@@ -472,6 +641,10 @@ extern "C" fem_status fem_op_qdata_host(fem_op *op, int64_t e, double *out) {
   if (!op || !out || e < 0 || e >= op->E) { fem_set_error("fem_op_qdata_host: invalid arguments"); return FEM_EINVAL; }
   const int nd = op->kind == FEM_DIFFUSION ? 6 : 1;
   const int64_t Q3 = (int64_t)op->Q * op->Q * op->Q;
+  {
+    const int rc = ensure_qdata64(op);
+    if (rc) return rc;
+  }
   FEM_CUDA_TRY(cudaMemcpyAsync(out, op->d_qdata + e * nd * Q3, sizeof(double) * nd * Q3,
                                cudaMemcpyDeviceToHost, op->stream()));
   FEM_CUDA_TRY(cudaStreamSynchronize(op->stream()));
@@ -481,6 +654,31 @@ extern "C" fem_status fem_op_qdata_host(fem_op *op, int64_t e, double *out) {
 extern "C" fem_status fem_op_rhs(fem_op *op, int which, double *b) {
   if (!op || !b || (which != 0 && which != 1)) { fem_set_error("fem_op_rhs: invalid arguments"); return FEM_EINVAL; }
   return fem_launch_rhs(op, which, b);
+}
+
+extern "C" fem_status fem_cg_checkpoint_size(const fem_op *op, int64_t *bytes) {
+  if (!op || !bytes) { fem_set_error("fem_cg_checkpoint_size: invalid arguments"); return FEM_EINVAL; }
+  *bytes = fem_cg_checkpoint_bytes(op);
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_cg_checkpoint(fem_op *op, void *state_host) {
+  if (!op || !state_host) { fem_set_error("fem_cg_checkpoint: invalid arguments"); return FEM_EINVAL; }
+  return fem_cg_checkpoint_save(op, state_host);
+}
+
+extern "C" fem_status fem_cg_restore(fem_op *op, const void *state_host) {
+  if (!op || !state_host) { fem_set_error("fem_cg_restore: invalid arguments"); return FEM_EINVAL; }
+  return fem_cg_checkpoint_restore(op, state_host);
+}
+
+extern "C" fem_status fem_cg_resume(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
+                                    fem_cg_stats *st) {
+  if (!op || !b || !x || !o || b == x || o->maxit < 0 || !(o->rtol >= 0.0)) {
+    fem_set_error("fem_cg_resume: invalid arguments");
+    return FEM_EINVAL;
+  }
+  return fem_cg_resume_run(op, b, x, o, st);
 }
 
 extern "C" fem_status fem_cg_solve(fem_op *op, const double *b, double *x, const fem_cg_opts *o,

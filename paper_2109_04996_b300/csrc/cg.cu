@@ -15,6 +15,7 @@
 // scalar until the solve ends (the paper's Laghos note: one dot product per
 // iteration brought back to the CPU; here none is).
 #include <math.h>
+#include <string.h>
 
 #include "fem_internal.h"
 
@@ -344,6 +345,151 @@ int fem_cg_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
   CgScalars out;
   FEM_CUDA_TRY(cudaMemcpyAsync(&out, w->sc, sizeof(out), cudaMemcpyDeviceToHost, s));
   FEM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (st) {
+    st->iterations = out.iter;
+    st->outer = 0;
+    st->status = out.status;
+    st->rnorm = sqrt(out.rr);
+    st->bnorm = sqrt(out.bb);
+    st->true_rel = -1.0;
+    st->fallback = 0;
+  }
+  return out.status;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / restore / resume of an interrupted CG solve.  A solve that
+// stopped at its iteration cap leaves, in the operator's workspace, the
+// iterate's residual r_k, z_k = M^-1 r_k, the previous direction p_{k-1} and
+// the scalars (r^T z, beta_k, ||b||^2, the iteration count): everything CG
+// needs besides x_k, which is the caller's.  Resuming forms p_k = z_k +
+// beta_k p_{k-1} and continues with the same kernels, so the resumed solve
+// is the uninterrupted one up to the order of the apply's atomic additions.
+
+namespace {
+struct CgCheckpointHeader {
+  char tag[8];      // "FEMCGCK1"
+  int64_t n;        // ncomp * N
+  int32_t pc;       // preconditioner of the interrupted solve
+  int32_t pad;
+};
+const char kCgTag[8] = {'F', 'E', 'M', 'C', 'G', 'C', 'K', '1'};
+
+__global__ void cg_resume_direction_kernel(const CgParams c) {
+  const double beta = c.sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    c.p[i] = c.z[i] + beta * c.p[i];
+    c.y[i] = 0.0;
+  }
+}
+}  // namespace
+
+int64_t fem_cg_checkpoint_bytes(const fem_op *op) {
+  return (int64_t)sizeof(CgCheckpointHeader) + (int64_t)sizeof(CgScalars) +
+         3 * (int64_t)sizeof(double) * op->N * op->ncomp;
+}
+
+int fem_cg_checkpoint_save(fem_op *op, void *host) {
+  CgWork *w = op->cg;
+  if (!w || w->dinv_pc < 0) {
+    fem_set_error("fem_cg_checkpoint: the operator has run no CG solve");
+    return FEM_EINVAL;
+  }
+  cudaStream_t s = op->stream();
+  CgCheckpointHeader h;
+  memcpy(h.tag, kCgTag, 8);
+  h.n = w->n; h.pc = w->dinv_pc; h.pad = 0;
+  char *out = (char *)host;
+  memcpy(out, &h, sizeof(h));
+  char *q = out + sizeof(h);
+  FEM_CUDA_TRY(cudaMemcpyAsync(q, w->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+  q += sizeof(CgScalars);
+  const size_t vb = sizeof(double) * (size_t)w->n;
+  FEM_CUDA_TRY(cudaMemcpyAsync(q, w->r, vb, cudaMemcpyDeviceToHost, s));
+  FEM_CUDA_TRY(cudaMemcpyAsync(q + vb, w->z, vb, cudaMemcpyDeviceToHost, s));
+  FEM_CUDA_TRY(cudaMemcpyAsync(q + 2 * vb, w->p, vb, cudaMemcpyDeviceToHost, s));
+  FEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return FEM_OK;
+}
+
+int fem_cg_checkpoint_restore(fem_op *op, const void *host) {
+  CgCheckpointHeader h;
+  memcpy(&h, host, sizeof(h));
+  if (memcmp(h.tag, kCgTag, 8) != 0 || h.n != op->N * op->ncomp ||
+      (h.pc != FEM_PC_NONE && h.pc != FEM_PC_JACOBI)) {
+    fem_set_error("fem_cg_restore: not a checkpoint of a CG solve on an operator of this size");
+    return FEM_EINVAL;
+  }
+  int rc = ensure_work(op);
+  if (rc) return rc;
+  CgWork *w = op->cg;
+  cudaStream_t s = op->stream();
+  const char *q = (const char *)host + sizeof(h);
+  FEM_CUDA_TRY(cudaMemcpyAsync(w->sc, q, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+  q += sizeof(CgScalars);
+  const size_t vb = sizeof(double) * (size_t)w->n;
+  FEM_CUDA_TRY(cudaMemcpyAsync(w->r, q, vb, cudaMemcpyHostToDevice, s));
+  FEM_CUDA_TRY(cudaMemcpyAsync(w->z, q + vb, vb, cudaMemcpyHostToDevice, s));
+  FEM_CUDA_TRY(cudaMemcpyAsync(w->p, q + 2 * vb, vb, cudaMemcpyHostToDevice, s));
+  cg_dinv_kernel<<<grid_for(w->n), kThreads, 0, s>>>(op->d_diag, op->mesh->d_dirichlet, op->N,
+                                                     w->n, h.pc, w->dinv);
+  FEM_CHECK_LAUNCH();
+  w->dinv_pc = h.pc;
+  FEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return FEM_OK;
+}
+
+int fem_cg_resume_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
+                      fem_cg_stats *st) {
+  CgWork *w = op->cg;
+  if (!w || w->dinv_pc < 0) {
+    fem_set_error("fem_cg_resume: no interrupted CG solve on this operator (run or restore one)");
+    return FEM_EINVAL;
+  }
+  if (o->precond != w->dinv_pc) {
+    fem_set_error("fem_cg_resume: preconditioner %d differs from the interrupted solve's %d",
+                  o->precond, w->dinv_pc);
+    return FEM_EINVAL;
+  }
+  cudaStream_t s = op->stream();
+  CgScalars sc;
+  FEM_CUDA_TRY(cudaMemcpyAsync(&sc, w->sc, sizeof(sc), cudaMemcpyDeviceToHost, s));
+  FEM_CUDA_TRY(cudaStreamSynchronize(s));
+  const bool capped = sc.done && sc.iter >= sc.maxit &&
+                      (sc.status == FEM_ENOCONV || (sc.status == FEM_OK && !(sc.tol2 > 0.0)));
+  if (!capped) {
+    fem_set_error("fem_cg_resume: the last solve did not stop at its iteration cap "
+                  "(status %d, %d of %d iterations)", sc.status, sc.iter, sc.maxit);
+    return FEM_EINVAL;
+  }
+  sc.maxit = sc.iter + o->maxit;
+  sc.tol2 = o->rtol * o->rtol * sc.bb;
+  sc.status = FEM_OK;
+  sc.done = 0;
+  if (sc.tol2 > 0.0 && sc.rr <= sc.tol2) sc.done = 1;   // already converged to the new rtol
+  if (o->maxit == 0) sc.done = 1;
+  FEM_CUDA_TRY(cudaMemcpyAsync(w->sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, s));
+  CgParams c = make_params(op, b, x, 0, 0);
+  if (!sc.done) {
+    cg_resume_direction_kernel<<<grid_for(c.n), kThreads, 0, s>>>(c);
+    FEM_CHECK_LAUNCH();
+    for (int it = 0; it < o->maxit; it++) {
+      int rc = launch_body(op, c, s);
+      if (rc) return rc;
+      if ((it & 7) == 7 || it == o->maxit - 1) {
+        int done = 0;
+        FEM_CUDA_TRY(cudaMemcpyAsync(&done, &w->sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (done) break;
+      }
+    }
+  }
+  CgScalars out;
+  FEM_CUDA_TRY(cudaMemcpyAsync(&out, w->sc, sizeof(out), cudaMemcpyDeviceToHost, s));
+  FEM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (!sc.done && out.status == FEM_OK && out.iter >= out.maxit && out.tol2 > 0.0 && out.rr > out.tol2)
+    out.status = FEM_ENOCONV;
   if (st) {
     st->iterations = out.iter;
     st->outer = 0;

@@ -6,6 +6,7 @@
 #include <string>
 
 #include "../../include/fem.h"
+#include "dw.cuh"
 
 #define FEM_MAX_P 9    // P = p + 1 <= 9
 #define FEM_MAX_Q 10   // q <= p + 2 <= 10
@@ -85,6 +86,8 @@ struct fem_op {
   float *d_B32 = nullptr, *d_Dq32 = nullptr;
   double *d_qdata = nullptr;      // [E][nd][Q^3]
   float *d_qdata32 = nullptr;     // FP32 copy (prec == FEM_F32)
+  dw *d_qdw = nullptr;            // double-word split (choices 8..10), made
+                                  // when one of them is first selected
   // trilinear Gauss diffusion only (P = 2), made when the trilinear body is
   // first selected (fem_ensure_qsum): line sums of the diagonal qdata
   // components, [E][3][Q^2]: sum over i of D00 at (j, k) (index j + Q k),
@@ -96,6 +99,7 @@ struct fem_op {
   // (a <= b), entry-major [P^3 (P^3 + 1) / 2][E]
   double *d_kel = nullptr;
   float *d_kel32 = nullptr;
+  dw *d_keldw = nullptr;          // double-word split of d_kel (choice 11)
   double *d_diag = nullptr;       // [N] scalar diagonal
   double *d_rff = nullptr;        // [M][4]
   int M = 0;
@@ -160,11 +164,20 @@ int fem_launch_apply_f64_shape(fem_op *op, const double *x, double *y, const int
 int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32_t *list,
                                int64_t nsel, double *dot_out, int choice, int bps,
                                const int *skip = nullptr);
+// the double-word bodies (choices 8..11) of the FP64 apply (apply_dw.cu)
+int fem_launch_apply_dw_shape(fem_op *op, const double *x, double *y, const int32_t *list,
+                              int64_t nsel, double *dot_out, int choice, int bps,
+                              const int *skip = nullptr);
 // Launch shape choices of an operator's apply: 0..2 the line-based body
 // (elements per block default, half, double), 3..5 the slab body, 6 the
 // trilinear body (Gauss diffusion at p = 1; at p = 2 the slab body's
 // default again), 7 the element-matrix body (Gauss diffusion at p = 1, 2);
-// the collocated mass operator (pointwise) has one.
+// the collocated mass operator (pointwise) has one.  The FP64 apply also
+// has the double-word bodies (FP64-accurate arithmetic on the FP32 pipe):
+// 8..10 the line-based body with the three elements-per-block sizes, 11 the
+// element-matrix body, 12..14 the line-based body with the next element
+// group's x gather carried one group ahead (scalar operators over whole
+// meshes; element lists and vector operators take 8..10's body).
 inline bool fem_has_elmat(int kind, bool colloc, int P) {
   return kind == FEM_DIFFUSION && !colloc && (P == 2 || P == 3);
 }
@@ -172,14 +185,33 @@ inline int fem_apply_choices(const fem_op *op) {
   if (fem_has_elmat(op->kind, op->colloc, op->P)) return 8;
   return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
 }
+constexpr int FEM_CHOICE_DW_LINES = 8;   // 8, 9, 10
+constexpr int FEM_CHOICE_DW_ELMAT = 11;
+constexpr int FEM_CHOICE_DW_PIPE = 12;   // 12, 13, 14
+constexpr int FEM_APPLY_CHOICES_MAX = 15;
+inline bool fem_choice_is_dw(int c) { return c >= FEM_CHOICE_DW_LINES && c < FEM_APPLY_CHOICES_MAX; }
 // Allocate and compute the trilinear body's line sums if op has none yet
 // (capi.cu); called where choice 6 is selected, outside stream capture.
 int fem_ensure_qsum(fem_op *op);
 
-// Choice c is a valid launch shape of op's apply (6 exists at P = 2 only).
-inline bool fem_apply_choice_valid(const fem_op *op, int c) {
+// Choice c is a valid launch shape of op's apply in precision prec (6
+// exists at P = 2 only; 8..11 in FP64 only).
+inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
+  if ((c >= FEM_CHOICE_DW_LINES && c < FEM_CHOICE_DW_ELMAT) ||
+      (c >= FEM_CHOICE_DW_PIPE && c < FEM_APPLY_CHOICES_MAX))
+    return prec == FEM_F64 && (op->kind == FEM_DIFFUSION || !op->colloc);
+  if (c == FEM_CHOICE_DW_ELMAT) return prec == FEM_F64 && fem_has_elmat(op->kind, op->colloc, op->P);
   return c >= 0 && c < fem_apply_choices(op) && !(c == 6 && op->P != 2);
 }
+// Make the data a launch choice of precision prec reads (FP64 qdata or
+// element matrices, the trilinear line sums, the double-word copies) if op
+// has none yet (capi.cu); called where the choice is selected, outside
+// stream capture.  Operators whose FP64 default is a double-word body
+// release their FP64 qdata and element matrices after set-up; these calls
+// rebuild them.
+int fem_ensure_choice_data(fem_op *op, int prec, int choice);
+// The FP64 qdata (recomputed from the mesh if released).
+int fem_ensure_qdata64(fem_op *op);
 // ---- p-multigrid internals used by the refined flexible CG (pmg.cu)
 struct fem_pmg;
 int fem_pmg_enqueue_vcycle32(fem_pmg *m, const float *r, float *z, cudaStream_t s);
@@ -193,6 +225,11 @@ int fem_launch_rhs(fem_op *op, int which, double *b);
 int fem_cg_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
                fem_cg_stats *st);
 void fem_cg_free(fem_op *op);
+int64_t fem_cg_checkpoint_bytes(const fem_op *op);
+int fem_cg_checkpoint_save(fem_op *op, void *host);
+int fem_cg_checkpoint_restore(fem_op *op, const void *host);
+int fem_cg_resume_run(fem_op *op, const double *b, double *x, const fem_cg_opts *o,
+                      fem_cg_stats *st);
 // ---- mixed precision (refine.cu)
 void fem_refine_free(fem_op *op);
 

@@ -11,6 +11,7 @@
 // Weights are FP32 masters; the GEMMs run in bf16 with FP32 accumulation
 // (tcgen05 tensor cores, mlp_tc.cuh), or in FP32 in the debug mode.  Training: mean squared error
 // against e_e / ||r_e|| for residual/error pairs of the plain solver, Adam.
+#include <cstdio>
 #include <math.h>
 #include <string.h>
 
@@ -321,6 +322,68 @@ extern "C" fem_status fem_mlp_params(fem_mlp *n, float *params_host, int64_t *np
     FEM_CUDA_TRY(cudaMemcpyAsync(params_host, n->p, sizeof(float) * n->np, cudaMemcpyDeviceToHost, n->stream));
     FEM_CUDA_TRY(cudaStreamSynchronize(n->stream));
   }
+  return FEM_OK;
+}
+
+// File layout of fem_mlp_save / fem_mlp_load: 8-byte tag "FEMMLP01", then
+// int32 n_in, n_h, n_out, mode, step, 0, int64 np, then np FP32 values each of
+// the parameters, Adam's first moments and Adam's second moments.
+static const char kMlpTag[8] = {'F', 'E', 'M', 'M', 'L', 'P', '0', '1'};
+
+extern "C" fem_status fem_mlp_save(fem_mlp *n, const char *path) {
+  if (!n || !path) { fem_set_error("fem_mlp_save: invalid arguments"); return FEM_EINVAL; }
+  std::vector<float> buf((size_t)3 * n->np);
+  const size_t pb = sizeof(float) * n->np;
+  FEM_CUDA_TRY(cudaMemcpyAsync(buf.data(), n->p, pb, cudaMemcpyDeviceToHost, n->stream));
+  FEM_CUDA_TRY(cudaMemcpyAsync(buf.data() + n->np, n->m, pb, cudaMemcpyDeviceToHost, n->stream));
+  FEM_CUDA_TRY(cudaMemcpyAsync(buf.data() + 2 * n->np, n->v, pb, cudaMemcpyDeviceToHost, n->stream));
+  FEM_CUDA_TRY(cudaStreamSynchronize(n->stream));
+  FILE *f = fopen(path, "wb");
+  if (!f) { fem_set_error("fem_mlp_save: cannot open %s", path); return FEM_EINVAL; }
+  const int32_t hdr[6] = {n->n_in, n->n_h, n->n_out, n->mode, n->step, 0};
+  const int64_t np = n->np;
+  bool ok = fwrite(kMlpTag, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            fwrite(&np, sizeof(np), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) { fem_set_error("fem_mlp_save: writing %s failed", path); return FEM_EINVAL; }
+  return FEM_OK;
+}
+
+extern "C" fem_status fem_mlp_load(const char *path, void *stream, fem_mlp **out) {
+  if (!path || !out) { fem_set_error("fem_mlp_load: invalid arguments"); return FEM_EINVAL; }
+  *out = nullptr;
+  FILE *f = fopen(path, "rb");
+  if (!f) { fem_set_error("fem_mlp_load: cannot open %s", path); return FEM_EINVAL; }
+  char tag[8];
+  int32_t hdr[6];
+  int64_t np = 0;
+  bool ok = fread(tag, 1, 8, f) == 8 && memcmp(tag, kMlpTag, 8) == 0 &&
+            fread(hdr, sizeof(hdr), 1, f) == 1 && fread(&np, sizeof(np), 1, f) == 1;
+  const int64_t want = ok ? (int64_t)hdr[1] * hdr[0] + hdr[1] + (int64_t)hdr[1] * hdr[1] + hdr[1] +
+                                (int64_t)hdr[2] * hdr[1] + hdr[2]
+                          : -1;
+  ok = ok && np == want && np > 0 && hdr[4] >= 0;
+  std::vector<float> buf;
+  if (ok) {
+    buf.resize((size_t)3 * np);
+    ok = fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  }
+  fclose(f);
+  if (!ok) { fem_set_error("fem_mlp_load: %s is not a saved network (tag, sizes or length)", path); return FEM_EINVAL; }
+  fem_mlp *n = nullptr;
+  int rc = fem_mlp_create(hdr[0], hdr[1], hdr[2], hdr[3], buf.data(), stream, &n);
+  if (rc) return rc;
+  const size_t pb = sizeof(float) * np;
+  cudaError_t e = cudaMemcpyAsync(n->m, buf.data() + np, pb, cudaMemcpyHostToDevice, n->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n->v, buf.data() + 2 * np, pb, cudaMemcpyHostToDevice, n->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  if (e != cudaSuccess) {
+    fem_mlp_destroy(n);
+    fem_set_error("fem_mlp_load: upload failed: %s", cudaGetErrorString(e));
+    return FEM_ECUDA;
+  }
+  n->step = hdr[4];
+  *out = n;
   return FEM_OK;
 }
 

@@ -16,7 +16,7 @@ namespace {
 
 const int kBpsCandidates[] = {1, 2, 3, 4, 6, 0};  // 0 = occupancy maximum
 
-int n_choices(const fem_op *op) { return fem_apply_choices(op); }
+int n_choices(const fem_op *) { return FEM_APPLY_CHOICES_MAX; }
 
 std::string cache_key(const fem_op *op, int prec) {
   int dev = 0, major = 0, minor = 0;
@@ -101,13 +101,13 @@ int launch(fem_op *op, int prec, void *x, void *y, int choice, int bps) {
 
 extern "C" fem_status fem_op_set_launch_shape(fem_op *op, int prec, int epb_choice,
                                               int blocks_per_sm) {
-  if (!op || (prec != FEM_F64 && prec != FEM_F32) || !fem_apply_choice_valid(op, epb_choice) ||
+  if (!op || (prec != FEM_F64 && prec != FEM_F32) || !fem_apply_choice_valid(op, prec, epb_choice) ||
       blocks_per_sm < 0) {
     fem_set_error("fem_op_set_launch_shape: invalid arguments");
     return FEM_EINVAL;
   }
-  if (epb_choice == 6) {
-    const int rc = fem_ensure_qsum(op);
+  {
+    const int rc = fem_ensure_choice_data(op, prec, epb_choice);
     if (rc) return rc;
   }
   op->tune_epb[prec] = epb_choice;
@@ -131,9 +131,9 @@ extern "C" fem_status fem_op_autotune(fem_op *op, int prec, const char *cache_pa
     entries = read_entries(cache_path);
     int c, b;
     double us;
-    if (lookup(entries, key, &c, &b, &us) && fem_apply_choice_valid(op, c) && b >= 0) {
-      if (c == 6) {
-        const int rc = fem_ensure_qsum(op);
+    if (lookup(entries, key, &c, &b, &us) && fem_apply_choice_valid(op, prec, c) && b >= 0) {
+      {
+        const int rc = fem_ensure_choice_data(op, prec, c);
         if (rc) return rc;
       }
       op->tune_epb[prec] = c;
@@ -160,8 +160,8 @@ extern "C" fem_status fem_op_autotune(fem_op *op, int prec, const char *cache_pa
   double best = 1e300;
   int best_c = 0, best_b = 0, ncand = 0;
   for (int c = 0; c < n_choices(op) && rc == FEM_OK; c++) {
-    if (!fem_apply_choice_valid(op, c)) continue;
-    if (c == 6 && (rc = fem_ensure_qsum(op))) break;
+    if (!fem_apply_choice_valid(op, prec, c)) continue;
+    if ((rc = fem_ensure_choice_data(op, prec, c))) break;
     for (int bps : kBpsCandidates) {
       // warm-up (also sets the kernel attributes)
       for (int w = 0; w < 2 && rc == FEM_OK; w++) rc = launch(op, prec, x, y, c, bps);

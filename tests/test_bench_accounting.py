@@ -45,12 +45,12 @@ def test_sum_factorized_orders_keep_the_general_count(bench, p):
 
 
 def test_traffic_ratios_are_near_the_algorithmic_bytes(bench):
-    # every order has a capture of its current default body, moving 1.0-1.15x
+    # every order has a capture of its current default body, moving 1.0-1.2x
     # the algorithmic bytes (scattered y sectors, shared-node x re-reads)
     total = 0.0
     for p in range(1, 9):
         r = bench.dram_ratio(p)
-        assert r is not None and 1.0 <= r <= 1.15, (p, r)
+        assert r is not None and 1.0 <= r <= 1.2, (p, r)
         n = fem_inputs.bp3_mesh_n(5e7, p)
         total += r * bench.body_algorithmic(p, n)[2]
     assert total > 0

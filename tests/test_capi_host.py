@@ -84,6 +84,22 @@ def test_mesh_create_rejects_bad_input_without_a_gpu(L):
     assert rc == 1
 
 
+def test_mesh_box_rejects_bad_arguments_without_a_gpu(L):
+    h = ctypes.c_void_p()
+    f = L.fem_mesh_box
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                  ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    assert f(0, 2, 2, 2, 0.1, 0, None, ctypes.byref(h)) == 1
+    assert f(9, 2, 2, 2, 0.1, 0, None, ctypes.byref(h)) == 1
+    assert f(2, 0, 2, 2, 0.1, 0, None, ctypes.byref(h)) == 1
+    assert f(2, 2, 2, 2, 0.5, 0, None, ctypes.byref(h)) == 1
+    assert f(2, 2, 2, 2, -0.1, 0, None, ctypes.byref(h)) == 1
+    assert b"perturb" in L.fem_last_error()
+    assert f(8, 2000, 2000, 2000, 0.0, 0, None, ctypes.byref(h)) == 1
+    assert b"int32" in L.fem_last_error()
+    assert f(2, 2, 2, 2, 0.1, 0, None, None) == 1
+
+
 def test_pmg_create_rejects_bad_hierarchies_without_a_gpu(L):
     h = ctypes.c_void_p()
     arr = (ctypes.c_void_p * 2)(None, None)

@@ -18,7 +18,7 @@ from paper_2109_04996_b300 import build as fembuild
 
 pytestmark = pytest.mark.gpu
 
-NROWS = 96
+NROWS = 1024
 
 
 @pytest.fixture(scope="module", autouse=True)
