@@ -327,6 +327,42 @@ fem_status fem_cg_restore(fem_op *op, const void *state_host);
 fem_status fem_cg_resume(fem_op *op, const double *b, double *x,
                          const fem_cg_opts *opts, fem_cg_stats *stats);
 
+/* ---------------------------------------------------------------- element-partitioned solve */
+
+/* Host callbacks through which fem_pcg_dist exchanges data with the other
+ * ranks (MPI, torch.distributed, ...).  Both return 0 on success; any other
+ * value ends the solve with FEM_EINVAL.
+ *  sum_interfaces(ctx, y): y is the caller's device work vector (the `y`
+ *    argument of fem_pcg_dist, ncomp*N local entries); add to every entry
+ *    of a node shared with other ranks their values of that node -- the
+ *    action of the subdomain restriction's transpose P^T (section "libCEED";
+ *    gslib's gather-scatter, section "Nek and MFEM").  The library has
+ *    synchronized its stream before the call.
+ *  allreduce(ctx, vals, count): vals is host memory; replace each of the
+ *    count values by its sum over all ranks. */
+typedef struct {
+  void *ctx;
+  int (*sum_interfaces)(void *ctx, double *y_dev);
+  int (*allreduce)(void *ctx, double *vals_host, int count);
+} fem_comm;
+
+/* One rank's part of Jacobi-PCG (opts->precond FEM_PC_JACOBI) or plain CG
+ * (FEM_PC_NONE) on an element-partitioned system: op is this rank's
+ * operator on its local mesh (its elements, local node ids), the global
+ * operator is the sum of the ranks' element operators.  owned: device [N]
+ * bytes, 1 on the local nodes this rank owns (every global node owned by
+ * exactly one rank); dot products sum over owned nodes and all-reduce.
+ * b, x: device [ncomp*N] local entries of the assembled right-hand side and
+ * of the solution (x is the initial guess unless opts->zero_guess);
+ * y: device [ncomp*N] work vector handed to sum_interfaces.  Dirichlet
+ * constraint and stopping test as fem_cg_solve (rtol relative to the global
+ * ||b||).  The applies and vector updates are the library's kernels; each
+ * iteration synchronizes the stream for one interface sum and two
+ * all-reduces.  Allocates 4 ncomp*N work vectors for the call. */
+fem_status fem_pcg_dist(fem_op *op, const uint8_t *owned, const double *b, double *x,
+                        double *y, const fem_cg_opts *opts, const fem_comm *comm,
+                        fem_cg_stats *stats);
+
 /* Mixed-precision solve of the same constrained system: FP64 iterative
  * refinement (classical; the paper fixes only the operator and CG) around an
  * inner Jacobi-PCG (or plain CG) that runs the FP32 apply on FP32 vectors

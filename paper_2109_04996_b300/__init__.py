@@ -56,6 +56,16 @@ class _CgStats(ctypes.Structure):
 
 _lib = None
 _VP = ctypes.c_void_p
+
+# fem_comm callbacks of fem_pcg_dist
+_CommSum = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_CommReduce = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_int)
+
+
+class _Comm(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("sum_interfaces", _CommSum),
+                ("allreduce", _CommReduce)]
 _I64 = ctypes.c_int64
 
 
@@ -98,6 +108,8 @@ def lib():
         "fem_op_rhs": [_VP, ctypes.c_int, _VP],
         "fem_cg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_solve_refined": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
+        "fem_pcg_dist": [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_Comm),
+                         ctypes.POINTER(_CgStats)],
         "fem_cg_checkpoint_size": [_VP, ctypes.POINTER(ctypes.c_int64)],
         "fem_cg_checkpoint": [_VP, _VP],
         "fem_cg_restore": [_VP, _VP],
@@ -779,3 +791,21 @@ class Pmg:
         if rc not in (0, 5):
             _check(rc)
         return _stats(st)
+
+
+def pcg_dist(op, owned, b, x, y, sum_interfaces, allreduce, precond=PC_JACOBI, rtol=1e-10,
+             maxit=10000, zero_guess=True):
+    """One rank's element-partitioned PCG (fem_pcg_dist); sum_interfaces and
+    allreduce are _CommSum / _CommReduce callbacks (paper_2109_04996_b300.dist
+    builds them from torch.distributed)."""
+    import torch
+    comm = _Comm(None, sum_interfaces, allreduce)
+    o = _CgOpts(precond, int(maxit), float(rtol), 0, 0.0, 0, 1 if zero_guess else 0)
+    st = _CgStats()
+    rc = lib().fem_pcg_dist(op._h, _vec(owned, torch.uint8, op.N, "owned"),
+                            _vec(b, torch.float64, op.n, "b"), _vec(x, torch.float64, op.n, "x"),
+                            _vec(y, torch.float64, op.n, "y"), ctypes.byref(o), ctypes.byref(comm),
+                            ctypes.byref(st))
+    if rc not in (0, 5):
+        _check(rc)
+    return _stats(st)

@@ -7,13 +7,15 @@ is a sum over the processes that share an interface node (gslib's
 gather-scatter), and CG's dot products are global sums (all-reduce).
 
 Here each rank owns a set of elements and the nodes they touch (local
-numbering); `Shard.apply` runs the local element operator (any callable on
-the local vector: the library's GPU operator in production, the FP64 oracle
-in the CPU tests) and then `Shard.sum_interfaces` adds the neighbouring
-ranks' contributions on shared nodes by point-to-point exchange, so every
-rank holds the assembled values of its nodes.  A node is owned by the lowest
-rank that touches it; dot products sum over owned nodes and all-reduce.
-Communication goes through torch.distributed (gloo on CPU, NCCL on GPUs).
+numbering).  This module holds the partition and the communication only:
+`Shard.sum_interfaces` adds the neighbouring ranks' contributions on shared
+nodes by point-to-point exchange (staged through host memory when the
+backend is gloo), and `Shard.pcg` runs the library's element-partitioned
+Jacobi-PCG (`fem_pcg_dist`), whose applies, vector updates and dot products
+are the library's kernels, handing it the interface sum and the scalar
+all-reduce as callbacks.  A node is owned by the lowest rank that touches
+it; dot products sum over owned nodes.  Communication goes through
+torch.distributed (gloo on CPU, NCCL on GPUs).
 """
 import numpy as np
 import torch
@@ -71,28 +73,27 @@ class Shard:
     # -- communication
     def sum_interfaces(self, y):
         """y (local, unassembled) += the neighbours' contributions on shared
-        nodes; every component [ncomp][N] is exchanged together."""
+        nodes; every component [ncomp][N] is exchanged together.  With the
+        gloo backend CUDA buffers are staged through host memory."""
         N = self.N
         yv = y.view(self.ncomp, N)
+        stage = y.is_cuda and dist.get_backend() == "gloo"
         sends, recvs, reqs = [], [], []
         for q, idx in self.neighbours:
-            buf = yv[:, idx].contiguous()
+            idx_y = idx.to(y.device) if idx.device != y.device else idx
+            buf = yv[:, idx_y].contiguous()
+            if stage:
+                buf = buf.cpu()
             out = torch.empty_like(buf)
             sends.append(buf)
-            recvs.append((idx, out))
+            recvs.append((idx_y, out))
             reqs.append(dist.isend(buf, q))
             reqs.append(dist.irecv(out, q))
         for r in reqs:
             r.wait()
-        for idx, out in recvs:
-            yv[:, idx] += out
+        for idx_y, out in recvs:
+            yv[:, idx_y] += out.to(y.device) if stage else out
         return y
-
-    def dot(self, u, v):
-        s = torch.sum(torch.where(self.owned, u * v, torch.zeros((), dtype=u.dtype, device=u.device)))
-        s = s.reshape(1).to(torch.float64)
-        dist.all_reduce(s)
-        return s.item()
 
     # -- operator
     def apply(self, local_apply, x):
@@ -107,31 +108,46 @@ class Shard:
         idx = torch.from_numpy(self.gnodes).to(xg.device)
         return torch.cat([xg[c * Ng + idx] for c in range(self.ncomp)]).to(self.device)
 
-    def pcg(self, local_apply, local_diag, b, rtol=1e-10, maxit=10000):
-        """Jacobi-PCG on the Dirichlet-constrained global system, distributed:
-        b is this rank's part of the right-hand side (assembled values);
-        local_diag the local (unassembled) diagonal, summed here.  Returns
-        (x, iterations) with x this rank's part of the solution."""
-        inner = self.inner
-        zero = torch.zeros((), dtype=b.dtype, device=b.device)
-        d = self.sum_interfaces(local_diag.clone())
-        dinv = torch.where(inner, 1.0 / torch.where(inner, d, torch.ones_like(d)), zero)
-        b = torch.where(inner, b, zero)
-        x = torch.zeros_like(b)
-        r = b.clone()
-        z = dinv * r
-        p = z.clone()
-        rz = self.dot(r, z)
-        bn = self.dot(b, b) ** 0.5
-        k = 0
-        while k < maxit and self.dot(r, r) ** 0.5 > rtol * bn:
-            Ap = torch.where(inner, self.apply(local_apply, torch.where(inner, p, zero)), zero)
-            alpha = rz / self.dot(p, Ap)
-            x += alpha * p
-            r -= alpha * Ap
-            z = dinv * r
-            rz_new = self.dot(r, z)
-            p = z + (rz_new / rz) * p
-            rz = rz_new
-            k += 1
-        return x, k
+    def owned_nodes(self, device="cuda"):
+        """[N] uint8: 1 on the local nodes this rank owns."""
+        return self.owned[:self.N].to(torch.uint8).to(device)
+
+    def pcg(self, op, b, x, precond=None, rtol=1e-10, maxit=10000, zero_guess=True):
+        """Jacobi-PCG (or plain CG, precond=PC_NONE) on the Dirichlet-
+        constrained global system through the library (fem_pcg_dist): op is
+        this rank's fem.Operator on local_mesh, b this rank's entries of the
+        assembled right-hand side, x its entries of the solution (in place).
+        Returns the library's statistics."""
+        import ctypes
+        import paper_2109_04996_b300 as fem
+        y = torch.zeros_like(b)
+        owned = self.owned_nodes(b.device)
+        errors = []
+
+        def cb_sum(ctx, ptr):
+            try:
+                self.sum_interfaces(y)
+                return 0
+            except Exception as e:  # noqa: BLE001 -- reported after the call
+                errors.append(e)
+                return 1
+
+        def cb_reduce(ctx, vals, count):
+            try:
+                t = torch.tensor([vals[i] for i in range(count)], dtype=torch.float64)
+                if dist.get_backend() != "gloo":
+                    t = t.to(b.device)
+                dist.all_reduce(t)
+                for i, v in enumerate(t.cpu().tolist()):
+                    vals[i] = v
+                return 0
+            except Exception as e:  # noqa: BLE001
+                errors.append(e)
+                return 1
+
+        st = fem.pcg_dist(op, owned, b, x, y, fem._CommSum(cb_sum), fem._CommReduce(cb_reduce),
+                          precond=fem.PC_JACOBI if precond is None else precond, rtol=rtol,
+                          maxit=maxit, zero_guess=zero_guess)
+        if errors:
+            raise errors[0]
+        return st
