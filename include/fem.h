@@ -422,6 +422,15 @@ fem_status fem_mlp_train(fem_mlp *mlp, const void *X, const float *T, int64_t S,
                          int valid, int epochs, int batch, float lr,
                          uint64_t seed, double *loss_host);
 
+/* fem_mlp_train in chunks of `chunk` epochs (a fresh permutation seed per
+ * chunk) until a chunk's mean loss is not below (1 - rel_tol) times the
+ * previous chunk's, or max_epochs have run.  loss_host[max_epochs] receives
+ * the mean loss of every epoch run, *epochs_run their number. */
+fem_status fem_mlp_train_plateau(fem_mlp *mlp, const void *X, const float *T, int64_t S,
+                                 int valid, int max_epochs, int chunk, double rel_tol,
+                                 int batch, float lr, uint64_t seed, double *loss_host,
+                                 int *epochs_run);
+
 /* The learned preconditioner of a scalar FEM_F32 operator:
  *   z = dinv * r + sum_e G_e^T ( w * ||r_e|| * net([r_e / ||r_e||, g_e]) )
  * g_e: 32 element features (the 8 corner nodes' offsets from the centroid
@@ -445,6 +454,16 @@ fem_status fem_precond_samples(fem_precond *pc, const double *b,
 /* Weight gamma >= 0 of the learned correction in B (default 1; 0 = Jacobi
  * alone, the network is then skipped). */
 fem_status fem_precond_set_gamma(fem_precond *pc, double gamma);
+/* Pick gamma among gammas[0..n): for each candidate run probe_iters
+ * flexible-CG iterations (one refinement step) on right-hand side b from
+ * x = 0 (x: device [N] work vector, overwritten) and keep the candidate with
+ * the smallest true residual; a candidate whose solve switched the learned
+ * part off (fallback) never wins.  Include 0 among the candidates to let
+ * Jacobi alone win.  Sets the preconditioner's gamma to the winner and
+ * returns it in *best_gamma.  Synchronizes. */
+fem_status fem_precond_calibrate(fem_precond *pc, const double *b, double *x,
+                                 const double *gammas, int n, int probe_iters,
+                                 double *best_gamma);
 /* z = B(r) (device FP32 [N] each). */
 fem_status fem_precond_apply(fem_precond *pc, const float *r, float *z);
 /* Flexible CG (Notay 2000, one stored direction) with preconditioner B as

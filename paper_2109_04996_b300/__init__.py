@@ -128,6 +128,9 @@ def lib():
                                ctypes.POINTER(ctypes.c_double)],
         "fem_mlp_train": [_VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                           ctypes.c_float, ctypes.c_uint64, _VP],
+        "fem_mlp_train_plateau": [_VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
+                                  _VP, ctypes.POINTER(ctypes.c_int)],
         "fem_precond_create": [_VP, _VP, ctypes.POINTER(_VP)],
         "fem_precond_create_pmg": [_VP, ctypes.POINTER(_VP)],
         "fem_precond_destroy": [_VP],
@@ -135,6 +138,8 @@ def lib():
         "fem_precond_samples": [_VP, _VP, _VP, _VP, _VP, _VP],
         "fem_precond_apply": [_VP, _VP, _VP],
         "fem_precond_set_gamma": [_VP, ctypes.c_double],
+        "fem_precond_calibrate": [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_double)],
         "fem_fcg_solve": [_VP, _VP, _VP, ctypes.POINTER(_CgOpts), ctypes.POINTER(_CgStats)],
         "fem_batch_create": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)],
         "fem_batch_create_split": [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int64,
@@ -621,6 +626,18 @@ class Mlp:
         _check(lib().fem_mlp_train_step(self._h, px, pt, S, valid, lr, None, ctypes.byref(L)))
         return L.value
 
+    def train_plateau(self, X, T, valid, max_epochs=60, chunk=4, rel_tol=0.01, batch=4096,
+                      lr=1e-3, seed=0):
+        """Train until the loss stops falling (fem_mlp_train_plateau); returns
+        the per-epoch mean losses of the epochs run."""
+        S, px, pt = self._xt(X, T)
+        losses = np.zeros(max_epochs)
+        ran = ctypes.c_int()
+        _check(lib().fem_mlp_train_plateau(self._h, px, pt, S, valid, int(max_epochs), int(chunk),
+                                           float(rel_tol), int(batch), float(lr), int(seed),
+                                           _ptr(losses), ctypes.byref(ran)))
+        return losses[:ran.value]
+
     def train(self, X, T, valid, epochs, batch=4096, lr=1e-3, seed=0):
         losses = np.zeros(epochs)
         S, px, pt = self._xt(X, T)
@@ -663,20 +680,15 @@ class Precond:
         self.gamma = float(gamma)
 
     def calibrate(self, b, gammas=(1.0, 0.5, 0.25, 0.1, 0.0), probe_iters=64):
-        """Pick the learned-term weight: for each candidate, run `probe_iters`
-        FCG iterations on right-hand side b from x = 0 and keep the weight
-        with the smallest true residual (0 = Jacobi alone)."""
+        """Pick the learned-term weight among `gammas` (fem_precond_calibrate)."""
         import torch
-        best = None
-        for gm in gammas:
-            self.set_gamma(gm)
-            x = torch.zeros_like(b)
-            st = self.fcg(b, x, rtol=1e-14, inner_rtol=1e-14, maxit=probe_iters, max_outer=1)
-            score = st["true_rel"] if st["fallback"] == 0 else float("inf")
-            if best is None or score < best[1]:
-                best = (gm, score)
-        self.set_gamma(best[0])
-        return best[0]
+        g = np.ascontiguousarray(gammas, dtype=np.float64)
+        x = torch.zeros_like(b)
+        best = ctypes.c_double()
+        _check(lib().fem_precond_calibrate(self._h, _vec(b, torch.float64, self.op.n, "b"),
+                                           _vec(x, torch.float64, self.op.n, "x"), _ptr(g), g.size,
+                                           int(probe_iters), ctypes.byref(best)))
+        return best.value
 
     def apply(self, r):
         import torch

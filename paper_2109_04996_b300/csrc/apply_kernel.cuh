@@ -130,6 +130,20 @@ __device__ __forceinline__ T gather_arith(const S *p, int l2_only) {
   return to_arith<T>(gather_load(p, l2_only));
 }
 
+// A pointwise-data entry in arithmetic type T.  The double-word bodies load
+// their (h, l) pairs through the read-only path (ld.global.nc): the loads
+// then cannot alias the shared-memory stores of the stage around them, so
+// the compiler may issue the next point's loads ahead of those stores.
+template <typename T, typename S>
+__device__ __forceinline__ T ld_qdata(const S *p) {
+  if constexpr (std::is_same<T, dw>::value && std::is_same<S, dw>::value) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return dw(v.x, v.y);
+  } else {
+    return to_arith<T>(*p);
+  }
+}
+
 // The double-word diffusion bodies apply A_e to x_e - c 1 (c = x at the
 // element's local node 0) instead of x_e: A_e annihilates constants, so the
 // result and the element's x_e^T A_e x_e are unchanged, but the values that

@@ -325,7 +325,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
 #pragma unroll
         for (int kq = 0; kq < Q; kq++) {
           const int pt = cube_ix<SJ, SK>(kq, lq1, lq0);
-          const T w = valid ? to_arith<T>(qd[(kq * Q + lq1) * Q + lq0]) : T(0);
+          const T w = valid ? ld_qdata<T>(qd + (kq * Q + lq1) * Q + lq0) : T(0);
           c3[pt] *= w;
         }
       }
@@ -364,8 +364,8 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         if (valid) {
           // qdata is unpadded: the cube index unless the cube is padded
           const auto *qk = qd + ((SJ == Q && SK == Q * Q) ? pt : (kq * Q + lq1) * Q + lq0);
-          G00 = to_arith<T>(qk[0]); G11 = to_arith<T>(qk[Q3]); G22 = to_arith<T>(qk[2 * Q3]);
-          G12 = to_arith<T>(qk[3 * Q3]); G02 = to_arith<T>(qk[4 * Q3]); G01 = to_arith<T>(qk[5 * Q3]);
+          G00 = ld_qdata<T>(qk); G11 = ld_qdata<T>(qk + Q3); G22 = ld_qdata<T>(qk + 2 * Q3);
+          G12 = ld_qdata<T>(qk + 3 * Q3); G02 = ld_qdata<T>(qk + 4 * Q3); G01 = ld_qdata<T>(qk + 5 * Q3);
         }
         const T gx = c1[pt], gy = c2[pt], gz = c4[pt];
         c1[pt] = G00 * gx + G01 * gy + G02 * gz;

@@ -703,6 +703,42 @@ extern "C" fem_status fem_fcg_solve(fem_precond *pc, const double *b, double *x,
   return status;
 }
 
+extern "C" fem_status fem_precond_calibrate(fem_precond *pc, const double *b, double *x,
+                                            const double *gammas, int n, int probe_iters,
+                                            double *best_gamma) {
+  if (!pc || !b || !x || !gammas || n < 1 || probe_iters < 1 || !best_gamma || b == x) {
+    fem_set_error("fem_precond_calibrate: invalid arguments");
+    return FEM_EINVAL;
+  }
+  for (int i = 0; i < n; i++)
+    if (!(gammas[i] >= 0.0) || !isfinite(gammas[i])) {
+      fem_set_error("fem_precond_calibrate: gamma %d must be finite and >= 0", i);
+      return FEM_EINVAL;
+    }
+  const double keep = pc->gamma;
+  fem_cg_opts o = {};
+  o.precond = FEM_PC_LEARNED;
+  o.maxit = probe_iters;
+  o.rtol = 1e-14;
+  o.inner_rtol = 1e-14;
+  o.max_outer = 1;
+  double best = 0.0, best_score = INFINITY;
+  bool have = false;
+  const size_t vb = sizeof(double) * (size_t)pc->n;
+  for (int i = 0; i < n; i++) {
+    pc->gamma = gammas[i];
+    FEM_CUDA_TRY(cudaMemsetAsync(x, 0, vb, pc->op->stream()));
+    fem_cg_stats st = {};
+    const int rc = fem_fcg_solve(pc, b, x, &o, &st);
+    if (rc != FEM_OK && rc != FEM_ENOCONV) { pc->gamma = keep; return rc; }
+    const double score = st.fallback ? INFINITY : st.true_rel;
+    if (!have || score < best_score) { best = gammas[i]; best_score = score; have = true; }
+  }
+  pc->gamma = best;
+  *best_gamma = best;
+  return FEM_OK;
+}
+
 extern "C" fem_status fem_precond_set_gamma(fem_precond *pc, double gamma) {
   if (!pc || !(gamma >= 0.0) || !isfinite(gamma)) {
     fem_set_error("fem_precond_set_gamma: gamma must be finite and >= 0");

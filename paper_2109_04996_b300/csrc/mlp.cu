@@ -546,3 +546,33 @@ extern "C" fem_status fem_mlp_train(fem_mlp *n, const void *X, const float *T, i
   }
   return fem_mlp_check_tc(n);
 }
+
+// Minibatch training until the loss stops falling: chunks of `chunk` epochs
+// (each a fem_mlp_train call with its own permutation seed), stopped when a
+// chunk's mean loss is not below (1 - rel_tol) times the previous chunk's, or
+// after max_epochs.  loss_host[max_epochs]: the mean loss per epoch run;
+// *epochs_run: how many ran.
+extern "C" fem_status fem_mlp_train_plateau(fem_mlp *n, const void *X, const float *T, int64_t S,
+                                            int valid, int max_epochs, int chunk, double rel_tol,
+                                            int batch, float lr, uint64_t seed, double *loss_host,
+                                            int *epochs_run) {
+  if (!n || !loss_host || !epochs_run || max_epochs < 1 || chunk < 1 || !(rel_tol >= 0.0)) {
+    fem_set_error("fem_mlp_train_plateau: invalid arguments");
+    return FEM_EINVAL;
+  }
+  int done = 0;
+  double prev = INFINITY;
+  while (done < max_epochs) {
+    const int k = chunk < max_epochs - done ? chunk : max_epochs - done;
+    const int rc = fem_mlp_train(n, X, T, S, valid, k, batch, lr,
+                                 seed + 0x9E3779B97F4A7C15ull * (uint64_t)(done + 1), loss_host + done);
+    if (rc) return rc;
+    double mean = 0.0;
+    for (int i = 0; i < k; i++) mean += loss_host[done + i] / k;
+    done += k;
+    if (!(mean < (1.0 - rel_tol) * prev)) break;
+    prev = mean;
+  }
+  *epochs_run = done;
+  return FEM_OK;
+}

@@ -266,16 +266,27 @@ def _train_learned(op, m, nrhs=6, ks=(2, 5, 10, 20, 40, 80), epochs=40, mode=0, 
             pc.samples(b, xs, xk, X[r0:r0 + m["E"]], T[r0:r0 + m["E"]])
             r0 += m["E"]
     batch = max(32, min(1024, (rows // 8) // 32 * 32))
-    losses = net.train(X, T, P3, epochs=epochs, batch=batch, lr=1e-3, seed=seed)
-    return net, pc, losses
+    scale = torch.sqrt(torch.mean(T[:, :P3].double() ** 2)).item()
+    T /= scale
+    losses = net.train_plateau(X, T, P3, max_epochs=epochs, chunk=4, rel_tol=0.01, batch=batch,
+                               lr=1e-3, seed=seed)
+    return net, pc, losses, scale
 
 
 def test_learned_fcg_reaches_fp64_accuracy_and_reports_its_gain():
     m, gm, op, rff = _kappa_problem(n=6, p=4)
-    net, pc, losses = _train_learned(op, m)
-    assert losses[-1] < losses[0]
+    net, pc, losses, scale = _train_learned(op, m)
+    # normalized targets (unit RMS over the P^3 outputs): predicting zero
+    # scores P^3 = 125; the network must explain a good part of that, and
+    # training stops at a plateau (or the epoch cap)
+    P3 = (m["p"] + 1) ** 3
+    assert losses[0] < 1.2 * P3 and losses[-1] < 0.8 * losses[0]
+    # the chunked training stopped at its plateau rule or at the 40-epoch cap
+    assert len(losses) == 40 or losses[-4:].mean() >= 0.99 * losses[-8:-4].mean()
     bval = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=998)).cuda()
-    gamma = pc.calibrate(bval)
+    gammas = [scale * g for g in (2.0, 1.0, 0.5, 0.25, 0.1)] + [0.0]
+    gamma = pc.calibrate(bval, gammas=gammas)
+    assert gamma in gammas
     b = torch.from_numpy(fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=999)).cuda()
     x = torch.zeros_like(b)
     st = pc.fcg(b, x, rtol=1e-10)
@@ -292,8 +303,9 @@ def test_learned_fcg_reaches_fp64_accuracy_and_reports_its_gain():
     print("\nlearned FCG: gamma %.2f, %d iterations (fallback %d) vs Jacobi %d: gain %.2fx;"
           " training loss %.3g -> %.3g" % (gamma, st["iterations"], st["fallback"],
                                           st0["iterations"], gain, losses[0], losses[-1]))
-    # calibration never picks a weight that loses to Jacobi on the probe by much
-    assert gain > 0.7
+    # what the bench reports: the calibrated preconditioner never loses to
+    # Jacobi-FCG beyond the iteration noise of FP32 inner solves
+    assert st["iterations"] <= 1.02 * st0["iterations"] + 2, (gamma, st, st0)
 
 
 def test_bad_network_falls_back_to_jacobi_and_still_converges():
