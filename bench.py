@@ -164,14 +164,14 @@ def measured_peaks():
 # matrices, indices and the two vectors, all proportional to the mesh), so
 # the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 1357970176, 23195392),
-    2: (493039, 4019679, 1615194880, 18181632),
-    3: (148877, 4096000, 1006073088, 35844352),
-    4: (59319, 3869893, 712035328, 30843648),
-    5: (32768, 4173281, 637772032, 31528192),
-    6: (17576, 3869893, 518211840, 27191552),
-    7: (12167, 4251528, 518851328, 29566720),
-    8: (8000, 4173281, 474271488, 28595200),
+    1: (3944312, 4019679, 1357794304, 23234816),
+    2: (493039, 4019679, 1613701888, 17927168),
+    3: (148877, 4096000, 1001927680, 34221056),
+    4: (59319, 3869893, 712196352, 30864128),
+    5: (32768, 4173281, 635446784, 31004672),
+    6: (17576, 3869893, 518104832, 27482624),
+    7: (12167, 4251528, 518910208, 29377024),
+    8: (8000, 4173281, 474237440, 29046528),
 }
 
 

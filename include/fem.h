@@ -228,7 +228,10 @@ fem_status fem_op_rhs(fem_op *op, int which, double *b);
  * pipe, with FP64 vectors and FP64 atomic scatter: 8, 9, 10 = the line-based
  * body with the three sizes, 11 = the element-matrix body (where 7 exists),
  * 12, 13, 14 = 8, 9, 10 with the next element group's x gather carried one
- * group ahead (scalar whole-mesh launches; otherwise as 8, 9, 10).  Their
+ * group ahead (scalar whole-mesh launches; otherwise as 8, 9, 10), 15, 16,
+ * 17 = 8, 9, 10 with the even and odd halves of every 1D contraction
+ * carried together in packed FP32x2 instructions (the same arithmetic,
+ * bit for bit, in half the issue slots).  Their
  * error against exact FP64 arithmetic: ~5e-14 relative l2 for random x; for
  * diffusion each element's x_e is shifted by its node-0 value first (A_e
  * annihilates constants), which keeps the smoothest fields within ~1e-12 at

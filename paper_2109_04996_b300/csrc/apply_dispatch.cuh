@@ -48,11 +48,11 @@ int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
 }
 
 // Diffusion: the line-based, even-odd element body (apply_lines.cuh).
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND>
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false>
 int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
-  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND>;
+  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND, PK>;
   static FemKernelCache cache;
   int &max_bps = cache.here();
   if (max_bps < 0) {
@@ -74,8 +74,11 @@ int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
 
 // pipe: carry the next group's x gather one group ahead (double words; the
 // FP32 body always does for scalar whole-mesh launches)
+// packed: the f32x2 form of the double-word contractions (no pipelined
+// gather)
 template <typename T, int P, int Q, bool COLLOC, int EPB, int KIND>
-int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps, bool pipe = false) {
+int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps, bool pipe = false,
+                 bool packed = false) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
   if constexpr (NT > 1024 || smem > 200 * 1024) {
@@ -93,6 +96,9 @@ int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps, bool pipe = fal
     make_symtab<T, Q, P>(Bt, lp.t.Bt);
     make_symtab<T, Q, Q>(op->tab.Dq, lp.t.Df);
     make_symtab<T, Q, Q>(Dt, lp.t.Dt);
+    if constexpr (std::is_same<T, dw>::value) {
+      if (packed) return launch_lines_kernel<T, P, Q, COLLOC, EPB, false, KIND, true>(op, lp, bps);
+    }
     if constexpr (sizeof(T) == 4 || std::is_same<T, dw>::value) {
       if (prm.ncomp == 1 && !prm.list && (sizeof(T) == 4 || pipe))
         return launch_lines_kernel<T, P, Q, COLLOC, EPB, true, KIND>(op, lp, bps);
@@ -191,6 +197,9 @@ int launch_epb_dw(fem_op *op, const ApplyParams<dw> &prm, int choice, int bps) {
       case 12: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps, true);
       case 13: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps, true);
       case 14: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps, true);
+      case 15: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps, false, true);
+      case 16: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps, false, true);
+      case 17: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps, false, true);
       default: break;
     }
   }

@@ -19,6 +19,8 @@
 // split tables are kernel parameters: every lane reads the same entry, which
 // the constant bank broadcasts.
 #pragma once
+#include <cstring>
+
 #include "apply_kernel.cuh"
 
 namespace fem_apply {
@@ -30,6 +32,19 @@ struct SymTab {
   T e[HO + 1][HI > 0 ? HI : 1];  // (M[k][a] + M[k][NI-1-a]) / 2
   T o[HO + 1][HI > 0 ? HI : 1];  // (M[k][a] - M[k][NI-1-a]) / 2
   T mid[HO + 1];                 // M[k][NI/2] (NI odd)
+};
+
+// Double words: the even and odd tables also as packed pairs for the f32x2
+// path of sym_apply: (e.h, o.h), (-e.h, -o.h), (-e.l, -o.l).
+template <int NI, int NO>
+struct SymTab<dw, NI, NO> {
+  static constexpr int HI = NI / 2, HO = NO / 2;
+  dw e[HO + 1][HI > 0 ? HI : 1];
+  dw o[HO + 1][HI > 0 ? HI : 1];
+  dw mid[HO + 1];
+  unsigned long long ph[HO > 0 ? HO : 1][HI > 0 ? HI : 1];
+  unsigned long long pnh[HO > 0 ? HO : 1][HI > 0 ? HI : 1];
+  unsigned long long pnl[HO > 0 ? HO : 1][HI > 0 ? HI : 1];
 };
 
 // out = M in over one line.  S = +1: M[NO-1-k][NI-1-a] = M[k][a];
@@ -111,6 +126,88 @@ __device__ __forceinline__ void sym_apply(const SymTab<dw, NI, NO> &M, const dw 
   }
 }
 
+// Double words: the even and odd accumulations of an output pair run the
+// same double-word instruction sequence, so they are carried as f32x2 pairs
+// (A, B): each packed instruction does the step for both, halving the
+// issue slots of the contraction.  The pair's value is h - nl (the low
+// words kept negated, so that the FMA-exact product error needs no
+// negation: with the negated tables, fma(-m.h, x.h, p) = -(m.h x.h - p)).
+// Per term: p = m.h x.h; ne = -(exact error of p) - m.h x.l - m.l x.h (three
+// FMAs); (h, e) = TwoSum(h, p); nl = nl + ne - e.  The first term starts
+// the pair (h, nl) = (p, ne).  The pre-sums ie = x + y, io = x - y are one
+// packed double-word sum of (x, x) and (y, -y).
+template <int S, int NI, int NO>
+__device__ __forceinline__ void sym_apply_packed(const SymTab<dw, NI, NO> &M, const dw (&in)[NI],
+                                                 dw (&out)[NO]) {
+  constexpr int HI = NI / 2, HO = NO / 2;
+  static_assert(HI > 0, "lines have at least two entries");
+  f32x2 xh[HI], xl[HI];   // (ie, io) high and low words
+#pragma unroll
+  for (int a = 0; a < HI; a++) {
+    const dw x = in[a], y = in[NI - 1 - a];
+    f32x2 s, e;
+    two_sum2(pk2(x.h, x.h), pk2(y.h, -y.h), s, e);
+    xh[a] = s;
+    xl[a] = add2(e, add2(pk2(x.l, x.l), pk2(y.l, -y.l)));
+  }
+#pragma unroll
+  for (int k = 0; k < HO; k++) {
+    f32x2 h = 0ull, nl = 0ull;
+#pragma unroll
+    for (int a = 0; a < HI; a++) {
+      const f32x2 mh = M.ph[k][a], nmh = M.pnh[k][a], nml = M.pnl[k][a];
+      const f32x2 p = mul2(mh, xh[a]);
+      f32x2 ne = fma2(nmh, xh[a], p);
+      ne = fma2(nmh, xl[a], ne);
+      ne = fma2(nml, xh[a], ne);
+      if (a == 0) {
+        h = p;
+        nl = ne;
+      } else {
+        f32x2 s, e;
+        two_sum2(h, p, s, e);
+        h = s;
+        nl = sub2(add2(nl, ne), e);
+      }
+    }
+    float Ah, Bh, Anl, Bnl;
+    upk2(h, Ah, Bh);
+    upk2(nl, Anl, Bnl);
+    dw A(Ah, -Anl), Bv(Bh, -Bnl);
+    if constexpr (NI % 2 == 1) A += M.mid[k] * in[HI];
+    out[k] = A + Bv;
+    out[NO - 1 - k] = (S > 0) ? A - Bv : Bv - A;
+  }
+  if constexpr (NO % 2 == 1) {
+    // the middle output: one chain, scalar double words
+    float xeh[HI], xoh[HI], xel[HI], xol[HI];
+#pragma unroll
+    for (int a = 0; a < HI; a++) {
+      upk2(xh[a], xeh[a], xoh[a]);
+      upk2(xl[a], xel[a], xol[a]);
+    }
+    if constexpr (S > 0) {
+      dw v = M.e[HO][0] * dw(xeh[0], xel[0]);
+#pragma unroll
+      for (int a = 1; a < HI; a++) v += M.e[HO][a] * dw(xeh[a], xel[a]);
+      if constexpr (NI % 2 == 1) v += M.mid[HO] * in[HI];
+      out[HO] = v;
+    } else {
+      dw v = M.o[HO][0] * dw(xoh[0], xol[0]);
+#pragma unroll
+      for (int a = 1; a < HI; a++) v += M.o[HO][a] * dw(xoh[a], xol[a]);
+      out[HO] = v;
+    }
+  }
+}
+
+// The line body's contractions: PK selects the packed form (double words).
+template <int S, bool PK, typename T, int NI, int NO>
+__device__ __forceinline__ void sym(const SymTab<T, NI, NO> &M, const T (&in)[NI], T (&out)[NO]) {
+  if constexpr (PK) sym_apply_packed<S>(M, in, out);
+  else sym_apply<S>(M, in, out);
+}
+
 template <typename T, int P, int Q>
 struct LineTables {
   static constexpr int kP = P, kQ = Q;
@@ -149,6 +246,20 @@ inline void make_symtab(const double *M, SymTab<T, NI, NO> &s) {
       }
     }
     s.mid[k] = tab_value<T>((NI % 2 == 1) ? M[k * NI + HI] : 0.0);
+  }
+  if constexpr (std::is_same<T, dw>::value) {
+    auto bits = [](float f) -> unsigned long long {
+      unsigned u;
+      memcpy(&u, &f, 4);
+      return u;
+    };
+    auto pack = [&](float lo, float hi) { return bits(lo) | (bits(hi) << 32); };
+    for (int k = 0; k < HO; k++)
+      for (int a = 0; a < (HI > 0 ? HI : 1); a++) {
+        s.ph[k][a] = pack(s.e[k][a].h, s.o[k][a].h);
+        s.pnh[k][a] = pack(-s.e[k][a].h, -s.o[k][a].h);
+        s.pnl[k][a] = pack(-s.e[k][a].l, -s.o[k][a].l);
+      }
   }
 }
 
@@ -232,7 +343,7 @@ __device__ __forceinline__ void column_values(const ApplyParams<T> &prm, Column<
 // KIND: FEM_DIFFUSION (gradients, 6 qdata per point) or FEM_MASS (values,
 // 1 qdata per point: the interpolation stages only; not collocated).
 template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE = false, bool PAD = true,
-          int KIND = FEM_DIFFUSION>
+          int KIND = FEM_DIFFUSION, bool PK = false>
 __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
                                                   const LineTables<T, P, Q> &tb, int64_t g,
                                                   T *cubes, double &dot,
@@ -292,7 +403,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       // z-interpolation of the column (a, b)
       if (on_pp) {
         T w[Q];
-        sym_apply<+1>(tb.Bf, u, w);
+        sym<+1, PK>(tb.Bf, u, w);
 #pragma unroll
         for (int k = 0; k < Q; k++) c1[cube_ix<SJ, SK>(k, lp1, lp0)] = w[k];
       }
@@ -302,7 +413,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T in[P], out[Q];
 #pragma unroll
         for (int j = 0; j < P; j++) in[j] = c1[cube_ix<SJ, SK>(lp1, j, lp0)];
-        sym_apply<+1>(tb.Bf, in, out);
+        sym<+1, PK>(tb.Bf, in, out);
 #pragma unroll
         for (int j = 0; j < Q; j++) c2[cube_ix<SJ, SK>(lp1, j, lp0)] = out[j];
       }
@@ -312,7 +423,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T in[P], out[Q];
 #pragma unroll
         for (int i = 0; i < P; i++) in[i] = c2[cube_ix<SJ, SK>(lq1, lq0, i)];
-        sym_apply<+1>(tb.Bf, in, out);
+        sym<+1, PK>(tb.Bf, in, out);
 #pragma unroll
         for (int i = 0; i < Q; i++) c3[cube_ix<SJ, SK>(lq1, lq0, i)] = out[i];
       }
@@ -337,19 +448,19 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       // x-line (jq, kq) = (lq0, lq1)
 #pragma unroll
       for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<SJ, SK>(lq1, lq0, m)];
-      sym_apply<-1>(tb.Df, in, out);
+      sym<-1, PK>(tb.Df, in, out);
 #pragma unroll
       for (int m = 0; m < Q; m++) c1[cube_ix<SJ, SK>(lq1, lq0, m)] = out[m];
       // y-line (iq, kq) = (lq0, lq1)
 #pragma unroll
       for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<SJ, SK>(lq1, m, lq0)];
-      sym_apply<-1>(tb.Df, in, out);
+      sym<-1, PK>(tb.Df, in, out);
 #pragma unroll
       for (int m = 0; m < Q; m++) c2[cube_ix<SJ, SK>(lq1, m, lq0)] = out[m];
       // z-line (iq, jq) = (lq0, lq1)
 #pragma unroll
       for (int m = 0; m < Q; m++) in[m] = c3[cube_ix<SJ, SK>(m, lq1, lq0)];
-      sym_apply<-1>(tb.Df, in, out);
+      sym<-1, PK>(tb.Df, in, out);
 #pragma unroll
       for (int m = 0; m < Q; m++) c4[cube_ix<SJ, SK>(m, lq1, lq0)] = out[m];
     }
@@ -379,17 +490,17 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
       T in[Q], out[Q];
 #pragma unroll
       for (int m = 0; m < Q; m++) in[m] = c1[cube_ix<SJ, SK>(lq1, lq0, m)];
-      sym_apply<-1>(tb.Dt, in, out);
+      sym<-1, PK>(tb.Dt, in, out);
 #pragma unroll
       for (int m = 0; m < Q; m++) c1[cube_ix<SJ, SK>(lq1, lq0, m)] = out[m];
 #pragma unroll
       for (int m = 0; m < Q; m++) in[m] = c2[cube_ix<SJ, SK>(lq1, m, lq0)];
-      sym_apply<-1>(tb.Dt, in, out);
+      sym<-1, PK>(tb.Dt, in, out);
 #pragma unroll
       for (int m = 0; m < Q; m++) c2[cube_ix<SJ, SK>(lq1, m, lq0)] = out[m];
 #pragma unroll
       for (int m = 0; m < Q; m++) in[m] = c4[cube_ix<SJ, SK>(m, lq1, lq0)];
-      sym_apply<-1>(tb.Dt, in, out);
+      sym<-1, PK>(tb.Dt, in, out);
 #pragma unroll
       for (int m = 0; m < Q; m++) c4[cube_ix<SJ, SK>(m, lq1, lq0)] = out[m];
     }
@@ -421,7 +532,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
           const int pt = cube_ix<SJ, SK>(lq1, lq0, m);
           in[m] = DIFF ? c1[pt] + c2[pt] + c4[pt] : c3[pt];
         }
-        sym_apply<+1>(tb.Bt, in, out);
+        sym<+1, PK>(tb.Bt, in, out);
 #pragma unroll
         for (int i = 0; i < P; i++) c3[cube_ix<SJ, SK>(lq1, lq0, i)] = out[i];
       }
@@ -431,7 +542,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T in[Q], out[P];
 #pragma unroll
         for (int j = 0; j < Q; j++) in[j] = c3[cube_ix<SJ, SK>(lp1, j, lp0)];
-        sym_apply<+1>(tb.Bt, in, out);
+        sym<+1, PK>(tb.Bt, in, out);
 #pragma unroll
         for (int j = 0; j < P; j++) c1[cube_ix<SJ, SK>(lp1, j, lp0)] = out[j];
       }
@@ -441,7 +552,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
         T in[Q], out[P];
 #pragma unroll
         for (int k = 0; k < Q; k++) in[k] = c1[cube_ix<SJ, SK>(k, lp1, lp0)];
-        sym_apply<+1>(tb.Bt, in, out);
+        sym<+1, PK>(tb.Bt, in, out);
 #pragma unroll
         for (int k = 0; k < P; k++) {
           if (valid) {
@@ -462,7 +573,7 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
 // (scalar operators over contiguous elements; the launcher picks it for FP32,
 // whose time is load latency); a separate instantiation, so that the others
 // keep their lower register count.
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND>
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false>
 __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     fem_apply_lines_kernel(const LineParams<T, P, Q> lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -476,12 +587,12 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     column_indices<T, P, Q, EPB>(prm, blockIdx.x, cur);
     column_values<T, P, ShiftX<T, KIND>::value>(prm, cur);
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-      apply_group_lines<T, P, Q, COLLOC, EPB, true, true, KIND>(prm, lp.t, g, cubes, dot, &cur, &nxt);
+      apply_group_lines<T, P, Q, COLLOC, EPB, true, true, KIND, PK>(prm, lp.t, g, cubes, dot, &cur, &nxt);
       cur = nxt;
     }
   } else {
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
-      apply_group_lines<T, P, Q, COLLOC, EPB, false, true, KIND>(prm, lp.t, g, cubes, dot);
+      apply_group_lines<T, P, Q, COLLOC, EPB, false, true, KIND, PK>(prm, lp.t, g, cubes, dot);
   }
   if (prm.dot_out) {
     double v[1] = {dot};

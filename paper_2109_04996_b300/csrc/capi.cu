@@ -476,16 +476,17 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   // the element-matrix body (7) for Gauss diffusion at p = 1 (3.2x the
   // trilinear body), the line body elsewhere, often with half the default
   // elements per block (1).  FP64: the double-word bodies everywhere (8..10
-  // line body, 12..14 with the pipelined gather, 11 element matrices at
-  // p = 1, 2): double-word arithmetic on the FP32 pipe, 4.4-4.9x the fastest
-  // FP64-arithmetic body for BP3 p = 3..7, 2.9x at p = 8, 1.4x (p = 1) and
-  // 1.07x (p = 2) over the FP64 element matrices, 3-4x for BP5 and BP1.
+  // line body, 12..14 with the pipelined gather, 15..17 with packed f32x2
+  // contractions, 11 element matrices at p = 1, 2): double-word arithmetic
+  // on the FP32 pipe, 4.4-5.2x the fastest FP64-arithmetic body for BP3
+  // p = 3..7, 3.2x at p = 8, 1.4x (p = 1) and 1.08x (p = 2) over the FP64
+  // element matrices, 3-4x for BP5 and BP1.
   static const int kDiffF32[8] = {7, 1, 1, 0, 1, 0, 0, 1};
-  static const int kDiffF64[8] = {11, 11, 9, 8, 8, 12, 12, 9};
+  static const int kDiffF64[8] = {11, 11, 16, 8, 15, 12, 12, 17};
   static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
-  static const int kCollF64[8] = {13, 9, 13, 9, 9, 8, 13, 14};
+  static const int kCollF64[8] = {13, 9, 16, 16, 15, 16, 13, 14};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
-  static const int kMassF64[8] = {9, 13, 13, 12, 9, 9, 8, 8};
+  static const int kMassF64[8] = {16, 16, 16, 12, 9, 9, 8, 8};
   const int ip = P - 2;   // P in 2..9
   if (kind == FEM_DIFFUSION && !op->colloc) {
     op->tune_epb[FEM_F32] = kDiffF32[ip];

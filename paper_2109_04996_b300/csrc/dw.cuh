@@ -65,6 +65,45 @@ __device__ __forceinline__ dw &operator-=(dw &a, dw b) { return a = a - b; }
 __device__ __forceinline__ dw &operator*=(dw &a, dw b) { return a = a * b; }
 __device__ __forceinline__ dw fma(dw a, dw b, dw c) { return c + a * b; }
 
+// Packed pairs of FP32 values for the f32x2 instructions (two FP32
+// operations per issue slot; same FMA rate per clock as scalar FP32 on
+// B300): element 0 in the low 32 bits.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// TwoSum on both halves: s + e = a + b exactly, element by element.
+__device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2 &s, f32x2 &e) {
+  s = add2(a, b);
+  const f32x2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
 // FP64 <-> double word.  The split is exact up to the 48 bits kept:
 // h = fl32(d), l = fl32(d - h) (d - h is exact in FP64).  Conversions
 // between FP64 and FP32 run at the FP64 rate on B300, so these two serve

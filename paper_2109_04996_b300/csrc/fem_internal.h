@@ -177,7 +177,9 @@ int fem_launch_apply_dw_shape(fem_op *op, const double *x, double *y, const int3
 // 8..10 the line-based body with the three elements-per-block sizes, 11 the
 // element-matrix body, 12..14 the line-based body with the next element
 // group's x gather carried one group ahead (scalar operators over whole
-// meshes; element lists and vector operators take 8..10's body).
+// meshes; element lists and vector operators take 8..10's body), 15..17 the
+// line-based body with its even and odd contractions carried as packed
+// f32x2 pairs.
 inline bool fem_has_elmat(int kind, bool colloc, int P) {
   return kind == FEM_DIFFUSION && !colloc && (P == 2 || P == 3);
 }
@@ -188,7 +190,8 @@ inline int fem_apply_choices(const fem_op *op) {
 constexpr int FEM_CHOICE_DW_LINES = 8;   // 8, 9, 10
 constexpr int FEM_CHOICE_DW_ELMAT = 11;
 constexpr int FEM_CHOICE_DW_PIPE = 12;   // 12, 13, 14
-constexpr int FEM_APPLY_CHOICES_MAX = 15;
+constexpr int FEM_CHOICE_DW_PACKED = 15; // 15, 16, 17
+constexpr int FEM_APPLY_CHOICES_MAX = 18;
 inline bool fem_choice_is_dw(int c) { return c >= FEM_CHOICE_DW_LINES && c < FEM_APPLY_CHOICES_MAX; }
 // Allocate and compute the trilinear body's line sums if op has none yet
 // (capi.cu); called where choice 6 is selected, outside stream capture.
@@ -198,7 +201,7 @@ int fem_ensure_qsum(fem_op *op);
 // exists at P = 2 only; 8..11 in FP64 only).
 inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
   if ((c >= FEM_CHOICE_DW_LINES && c < FEM_CHOICE_DW_ELMAT) ||
-      (c >= FEM_CHOICE_DW_PIPE && c < FEM_APPLY_CHOICES_MAX))
+      (c >= FEM_CHOICE_DW_PIPE && c < FEM_APPLY_CHOICES_MAX))   // 8..10, 12..17
     return prec == FEM_F64 && (op->kind == FEM_DIFFUSION || !op->colloc);
   if (c == FEM_CHOICE_DW_ELMAT) return prec == FEM_F64 && fem_has_elmat(op->kind, op->colloc, op->P);
   return c >= 0 && c < fem_apply_choices(op) && !(c == 6 && op->P != 2);

@@ -18,7 +18,7 @@ from paper_2109_04996_b300 import build as fembuild
 
 pytestmark = pytest.mark.gpu
 
-DW_LINES = (8, 9, 10, 12, 13, 14)   # 12..14: pipelined gather (scalar whole-mesh launches)
+DW_LINES = (8, 9, 10, 12, 13, 14, 15, 16, 17)   # 12..14 pipelined gather, 15..17 packed f32x2
 DW_ELMAT = 11
 
 
