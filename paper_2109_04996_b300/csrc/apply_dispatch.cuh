@@ -158,12 +158,19 @@ int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
     return FEM_EINVAL;
   }
   constexpr int NT = kElmatThreads;
-  auto kern = fem_apply_elmat_kernel<T, P>;
+  // double words at P = 3: x_e in shared memory (fem_apply_elmat_xs_kernel)
+  constexpr bool XS = std::is_same<T, dw>::value && P == 3;
+  constexpr size_t smem = XS ? sizeof(dw) * (size_t)NT * P * P * P : 0;
+  auto kern = [] {
+    if constexpr (XS) return fem_apply_elmat_xs_kernel<P>;
+    else return fem_apply_elmat_kernel<T, P>;
+  }();
   static FemKernelCache cache;
   int &max_bps = cache.here();
   if (max_bps < 0) {
+    if (smem > 0) FEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0));
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     max_bps = per_sm < 1 ? 1 : per_sm;
   }
   const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
@@ -172,7 +179,7 @@ int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
   if (grid > nblk) grid = nblk;
   if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, NT, 0, op->stream()>>>(ep);
+  kern<<<(unsigned)grid, NT, smem, op->stream()>>>(ep);
   FEM_CHECK_LAUNCH();
   return FEM_OK;
 }
