@@ -231,14 +231,17 @@ fem_status fem_op_rhs(fem_op *op, int which, double *b);
  * group ahead (scalar whole-mesh launches; otherwise as 8, 9, 10), 15, 16,
  * 17 = 8, 9, 10 with the even and odd halves of every 1D contraction
  * carried together in packed FP32x2 instructions (the same arithmetic,
- * bit for bit, in half the issue slots).  Their
+ * bit for bit, in half the issue slots), 18, 19, 20 = 15, 16, 17 with an L2
+ * bulk prefetch of the next element group's qdata and node ids, 21, 22,
+ * 23 = 18, 19, 20 with the pipelined gather of 12, 13, 14 (same results as
+ * 15, 16, 17 up to the order of the atomic additions).  Their
  * error against exact FP64 arithmetic: ~5e-14 relative l2 for random x; for
  * diffusion each element's x_e is shifted by its node-0 value first (A_e
  * annihilates constants), which keeps the smoothest fields within ~1e-12 at
  * 8e6 DOFs; x values below 2^-74 in magnitude lose the low word (FP32's
  * exponent range).  blocks_per_sm: resident blocks per SM (0 = the occupancy
  * maximum).  Defaults: the fastest choice of a sweep at 8e6 DOFs per order
- * and operator type; FP64: the double-word bodies; FP32: 7 for Gauss
+ * and operator type (BP3 FP64 at 5e7 DOFs); FP64: the double-word bodies; FP32: 7 for Gauss
  * diffusion at p = 1, the line body elsewhere. */
 typedef struct {
   int epb_choice;

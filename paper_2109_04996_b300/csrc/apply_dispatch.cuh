@@ -48,11 +48,12 @@ int launch_shape(fem_op *op, const ApplyParams<T> &prm, int bps) {
 }
 
 // Diffusion: the line-based, even-odd element body (apply_lines.cuh).
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false>
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
+          bool PF = false>
 int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
-  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND, PK>;
+  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
   static FemKernelCache cache;
   int &max_bps = cache.here();
   if (max_bps < 0) {
@@ -74,11 +75,12 @@ int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
 
 // pipe: carry the next group's x gather one group ahead (double words; the
 // FP32 body always does for scalar whole-mesh launches)
-// packed: the f32x2 form of the double-word contractions (no pipelined
-// gather)
+// packed: the f32x2 form of the double-word contractions
+// pf: L2 bulk prefetch of the next group's qdata and node ids (double words,
+// packed only)
 template <typename T, int P, int Q, bool COLLOC, int EPB, int KIND>
 int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps, bool pipe = false,
-                 bool packed = false) {
+                 bool packed = false, bool pf = false) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
   if constexpr (NT > 1024 || smem > 200 * 1024) {
@@ -97,6 +99,11 @@ int launch_lines(fem_op *op, const ApplyParams<T> &prm, int bps, bool pipe = fal
     make_symtab<T, Q, Q>(op->tab.Dq, lp.t.Df);
     make_symtab<T, Q, Q>(Dt, lp.t.Dt);
     if constexpr (std::is_same<T, dw>::value) {
+      if (packed && pf) {
+        if (pipe && prm.ncomp == 1 && !prm.list)
+          return launch_lines_kernel<T, P, Q, COLLOC, EPB, true, KIND, true, true>(op, lp, bps);
+        return launch_lines_kernel<T, P, Q, COLLOC, EPB, false, KIND, true, true>(op, lp, bps);
+      }
       if (packed) return launch_lines_kernel<T, P, Q, COLLOC, EPB, false, KIND, true>(op, lp, bps);
     }
     if constexpr (sizeof(T) == 4 || std::is_same<T, dw>::value) {
@@ -157,12 +164,13 @@ int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
     fem_set_error("apply: the element-matrix body needs the operator's element matrices");
     return FEM_EINVAL;
   }
-  constexpr int NT = kElmatThreads;
-  // double words at P = 3: x_e in shared memory (fem_apply_elmat_xs_kernel)
-  constexpr bool XS = std::is_same<T, dw>::value && P == 3;
-  constexpr size_t smem = XS ? sizeof(dw) * (size_t)NT * P * P * P : 0;
+  // double words at P = 3: the layered body (three warps per 32 elements)
+  constexpr bool LAYERS = std::is_same<T, dw>::value && P == 3;
+  constexpr int NT = LAYERS ? kLayerThreads : kElmatThreads;
+  constexpr int PER_BLOCK = LAYERS ? 32 * kLayerGroups : kElmatThreads;
+  constexpr size_t smem = 0;
   auto kern = [] {
-    if constexpr (XS) return fem_apply_elmat_xs_kernel<P>;
+    if constexpr (LAYERS) return fem_apply_elmat_layers_kernel<P>;
     else return fem_apply_elmat_kernel<T, P>;
   }();
   static FemKernelCache cache;
@@ -174,7 +182,7 @@ int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
     max_bps = per_sm < 1 ? 1 : per_sm;
   }
   const int use = (bps <= 0 || bps > max_bps) ? max_bps : bps;
-  const int64_t nblk = (prm.nsel + NT - 1) / NT;
+  const int64_t nblk = (prm.nsel + PER_BLOCK - 1) / PER_BLOCK;
   int64_t grid = (int64_t)op->nsm * use;
   if (grid > nblk) grid = nblk;
   if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
@@ -207,6 +215,12 @@ int launch_epb_dw(fem_op *op, const ApplyParams<dw> &prm, int choice, int bps) {
       case 15: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps, false, true);
       case 16: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps, false, true);
       case 17: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps, false, true);
+      case 18: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps, false, true, true);
+      case 19: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps, false, true, true);
+      case 20: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps, false, true, true);
+      case 21: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 0>::value, KIND>(op, prm, bps, true, true, true);
+      case 22: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 1>::value, KIND>(op, prm, bps, true, true, true);
+      case 23: return launch_lines<dw, P, Q, COLLOC, EpbChoice<Q, 2>::value, KIND>(op, prm, bps, true, true, true);
       default: break;
     }
   }

@@ -220,6 +220,24 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Bulk prefetch of [p, p + bytes) into L2 (one instruction, nothing to wait
+// for).  The range is shrunk to whole 16-byte units inside it (start rounded
+// up, end rounded down), so that it never leaves the buffer it came from.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = (a + 15) & ~(uintptr_t)15, hi = (a + bytes) & ~(uintptr_t)15;
+  if (hi <= lo) return;
+  size_t n = hi - lo;
+  uintptr_t s = lo;
+  // in pieces of at most 64 KB
+  while (n > 0) {
+    const unsigned piece = n > 65536 ? 65536u : (unsigned)n;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(s), "r"(piece) : "memory");
+    s += piece;
+    n -= piece;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void atomic_add(T *a, T v) { atomicAdd(a, v); }
 __device__ __forceinline__ void atomic_add(double *a, dw v) { atomicAdd(a, dw_to_double_int(v)); }

@@ -342,8 +342,12 @@ __device__ __forceinline__ void column_values(const ApplyParams<T> &prm, Column<
 // its values after the gradient stage.
 // KIND: FEM_DIFFUSION (gradients, 6 qdata per point) or FEM_MASS (values,
 // 1 qdata per point: the interpolation stages only; not collocated).
+// PF (contiguous elements): thread 0 starts an L2 bulk prefetch of the
+// next group's qdata (and of its element node ids, two groups ahead when
+// PIPE loads the next group's ids here), so that the pointwise stage's
+// qdata loads hit L2.
 template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE = false, bool PAD = true,
-          int KIND = FEM_DIFFUSION, bool PK = false>
+          int KIND = FEM_DIFFUSION, bool PK = false, bool PF = false>
 __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
                                                   const LineTables<T, P, Q> &tb, int64_t g,
                                                   T *cubes, double &dot,
@@ -377,6 +381,20 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
   // this thread's share of x.y over the group (see DotAcc), added to the
   // FP64 `dot` once
   DotAcc<T> dl;
+  if constexpr (PF) {
+    if (threadIdx.x == 0 && !prm.list) {
+      constexpr int NQD = DIFF ? 6 : 1;
+      const int64_t eq = (g + gridDim.x) * EPB, ei = (g + (PIPE ? 2 : 1) * (int64_t)gridDim.x) * EPB;
+      if (eq < prm.nsel) {
+        const int64_t ne = prm.nsel - eq < EPB ? prm.nsel - eq : EPB;
+        prefetch_l2(prm.qdata + eq * NQD * Q3, (size_t)ne * NQD * Q3 * sizeof(*prm.qdata));
+      }
+      if (ei < prm.nsel) {
+        const int64_t ne = prm.nsel - ei < EPB ? prm.nsel - ei : EPB;
+        prefetch_l2(prm.elem_nodes + ei * P3, (size_t)ne * P3 * sizeof(int32_t));
+      }
+    }
+  }
   if constexpr (PIPE) column_indices<T, P, Q, EPB>(prm, g + gridDim.x, *nxt);
   for (int c = 0; c < prm.ncomp; c++) {
     const auto *xc = prm.x + c * N;
@@ -573,7 +591,8 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
 // (scalar operators over contiguous elements; the launcher picks it for FP32,
 // whose time is load latency); a separate instantiation, so that the others
 // keep their lower register count.
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false>
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
+          bool PF = false>
 __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     fem_apply_lines_kernel(const LineParams<T, P, Q> lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -587,12 +606,12 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     column_indices<T, P, Q, EPB>(prm, blockIdx.x, cur);
     column_values<T, P, ShiftX<T, KIND>::value>(prm, cur);
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-      apply_group_lines<T, P, Q, COLLOC, EPB, true, true, KIND, PK>(prm, lp.t, g, cubes, dot, &cur, &nxt);
+      apply_group_lines<T, P, Q, COLLOC, EPB, true, true, KIND, PK, PF>(prm, lp.t, g, cubes, dot, &cur, &nxt);
       cur = nxt;
     }
   } else {
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x)
-      apply_group_lines<T, P, Q, COLLOC, EPB, false, true, KIND, PK>(prm, lp.t, g, cubes, dot);
+      apply_group_lines<T, P, Q, COLLOC, EPB, false, true, KIND, PK, PF>(prm, lp.t, g, cubes, dot);
   }
   if (prm.dot_out) {
     double v[1] = {dot};

@@ -153,6 +153,17 @@ __global__ void f64_to_dw_kernel(const double *a, dw *b, int64_t n) {
     b[i] = dw_from_double(a[i]);
 }
 
+// P = 3: the double-word element matrices in the layered body's entry order
+// (fem_elmat_layer_src maps it to the row-packed FP64 order).
+__global__ void kel_layers_dw_kernel(const double *a, dw *b, int64_t E) {
+  const int64_t n = 378 * E;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / E, e = i - k * E;
+    b[i] = dw_from_double(a[(int64_t)fem_elmat_layer_src((int)k) * E + e]);
+  }
+}
+
 // The FP64 qdata, recomputed from the mesh when it was released.
 int ensure_qdata64(fem_op *op) {
   if (op->d_qdata) return FEM_OK;
@@ -190,7 +201,10 @@ int ensure_keldw(fem_op *op) {
   const int P3 = op->P * op->P * op->P;
   const size_t nk = (size_t)op->E * (size_t)(P3 * (P3 + 1) / 2);
   if ((rc = dev_alloc(&op->d_keldw, nk, &op->bytes))) return rc;
-  if (nk > 0) f64_to_dw_kernel<<<148 * 8, 256, 0, op->stream()>>>(op->d_kel, op->d_keldw, (int64_t)nk);
+  if (nk > 0) {
+    if (op->P == 3) kel_layers_dw_kernel<<<148 * 8, 256, 0, op->stream()>>>(op->d_kel, op->d_keldw, op->E);
+    else f64_to_dw_kernel<<<148 * 8, 256, 0, op->stream()>>>(op->d_kel, op->d_keldw, (int64_t)nk);
+  }
   FEM_CHECK_LAUNCH();
   return FEM_OK;
 }
@@ -471,20 +485,23 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   const int64_t Q3 = (int64_t)Q * Q * Q;
   const int nd = kind == FEM_DIFFUSION ? 6 : 1;
   // Default launch shapes: the fastest choice (fem_apply_choices) of a
-  // sweep of every choice at 8e6 DOFs on a B300, per P = p + 1 (index P - 2):
-  // BP3 (Gauss q = p + 2), BP5 (collocated) and BP1 (Gauss mass).  FP32:
-  // the element-matrix body (7) for Gauss diffusion at p = 1 (3.2x the
-  // trilinear body), the line body elsewhere, often with half the default
-  // elements per block (1).  FP64: the double-word bodies everywhere (8..10
-  // line body, 12..14 with the pipelined gather, 15..17 with packed f32x2
-  // contractions, 11 element matrices at p = 1, 2): double-word arithmetic
+  // sweep of every choice at 8e6 DOFs on a B300 (the FP64 double-word
+  // choices of BP3 at 5e7 DOFs, BP5 p = 7 at 3e7: median of four interleaved
+  // rounds), per P = p + 1 (index P - 2): BP3 (Gauss q = p + 2), BP5
+  // (collocated) and BP1 (Gauss mass).  FP32: the element-matrix body (7)
+  // for Gauss diffusion at p = 1 (3.2x the trilinear body), the line body
+  // elsewhere, often with half the default elements per block (1).  FP64:
+  // the double-word bodies everywhere (8..10 line body, 12..14 with the
+  // pipelined gather, 15..17 with packed f32x2 contractions, 18..23 packed
+  // with the next group's qdata prefetched into L2 -- 21..23 also with the
+  // pipelined gather --, 11 element matrices at p = 1, 2): double-word arithmetic
   // on the FP32 pipe, 4.4-5.2x the fastest FP64-arithmetic body for BP3
   // p = 3..7, 3.2x at p = 8, 1.4x (p = 1) and 1.08x (p = 2) over the FP64
   // element matrices, 3-4x for BP5 and BP1.
   static const int kDiffF32[8] = {7, 1, 1, 0, 1, 0, 0, 1};
-  static const int kDiffF64[8] = {11, 11, 16, 8, 15, 12, 12, 17};
+  static const int kDiffF64[8] = {11, 11, 16, 8, 21, 12, 12, 20};
   static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
-  static const int kCollF64[8] = {13, 9, 16, 16, 15, 16, 13, 14};
+  static const int kCollF64[8] = {13, 9, 19, 16, 15, 21, 19, 14};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
   static const int kMassF64[8] = {16, 16, 16, 12, 9, 9, 8, 8};
   const int ip = P - 2;   // P in 2..9

@@ -183,6 +183,31 @@ int fem_launch_apply_dw_shape(fem_op *op, const double *x, double *y, const int3
 inline bool fem_has_elmat(int kind, bool colloc, int P) {
   return kind == FEM_DIFFUSION && !colloc && (P == 2 || P == 3);
 }
+// Element matrices at P = 3 in the double-word layered body's entry order
+// (apply_elmat.cuh): the upper triangles of the three diagonal layer blocks
+// (45 entries each, row-major, i <= j), then the off-diagonal blocks K of
+// layer t against layer t+1 mod 3 (81 entries each, row-major).  Returns
+// the index of layered entry n in the row-packed upper triangle (a <= b).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int fem_elmat_layer_src(int n) {
+  constexpr int P3 = 27, L = 9, NL = 3, TRI = L * (L + 1) / 2;
+  int a, b;
+  if (n < NL * TRI) {
+    const int t = n / TRI;
+    int r = n - t * TRI, i = 0;
+    while (r >= L - i) { r -= L - i; i++; }
+    a = L * t + i;
+    b = L * t + i + r;
+  } else {
+    const int m = n - NL * TRI, t = m / (L * L), ij = m - t * L * L;
+    a = L * t + ij / L;
+    b = L * ((t + 1) % NL) + ij % L;
+  }
+  if (a > b) { const int u = a; a = b; b = u; }
+  return a * P3 - a * (a - 1) / 2 + (b - a);
+}
 inline int fem_apply_choices(const fem_op *op) {
   if (fem_has_elmat(op->kind, op->colloc, op->P)) return 8;
   return (op->kind == FEM_DIFFUSION || !op->colloc) ? 6 : 1;
@@ -191,7 +216,8 @@ constexpr int FEM_CHOICE_DW_LINES = 8;   // 8, 9, 10
 constexpr int FEM_CHOICE_DW_ELMAT = 11;
 constexpr int FEM_CHOICE_DW_PIPE = 12;   // 12, 13, 14
 constexpr int FEM_CHOICE_DW_PACKED = 15; // 15, 16, 17
-constexpr int FEM_APPLY_CHOICES_MAX = 18;
+constexpr int FEM_CHOICE_DW_PF = 18;     // 18, 19, 20 (21, 22, 23: with the pipelined gather)
+constexpr int FEM_APPLY_CHOICES_MAX = 24;
 inline bool fem_choice_is_dw(int c) { return c >= FEM_CHOICE_DW_LINES && c < FEM_APPLY_CHOICES_MAX; }
 // Allocate and compute the trilinear body's line sums if op has none yet
 // (capi.cu); called where choice 6 is selected, outside stream capture.
@@ -201,7 +227,7 @@ int fem_ensure_qsum(fem_op *op);
 // exists at P = 2 only; 8..11 in FP64 only).
 inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
   if ((c >= FEM_CHOICE_DW_LINES && c < FEM_CHOICE_DW_ELMAT) ||
-      (c >= FEM_CHOICE_DW_PIPE && c < FEM_APPLY_CHOICES_MAX))   // 8..10, 12..17
+      (c >= FEM_CHOICE_DW_PIPE && c < FEM_APPLY_CHOICES_MAX))   // 8..10, 12..23
     return prec == FEM_F64 && (op->kind == FEM_DIFFUSION || !op->colloc);
   if (c == FEM_CHOICE_DW_ELMAT) return prec == FEM_F64 && fem_has_elmat(op->kind, op->colloc, op->P);
   return c >= 0 && c < fem_apply_choices(op) && !(c == 6 && op->P != 2);

@@ -18,7 +18,7 @@ from paper_2109_04996_b300 import build as fembuild
 
 pytestmark = pytest.mark.gpu
 
-DW_LINES = (8, 9, 10, 12, 13, 14, 15, 16, 17)   # 12..14 pipelined gather, 15..17 packed f32x2
+DW_LINES = (8, 9, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22, 23)   # 12..14 pipelined gather, 15..17 packed f32x2, 18..23 packed with L2 prefetch (21..23 and the pipelined gather)
 DW_ELMAT = 11
 
 
