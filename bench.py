@@ -164,13 +164,13 @@ def measured_peaks():
 # matrices, indices and the two vectors, all proportional to the mesh), so
 # the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 1357794304, 23234816),
-    2: (493039, 4019679, 1613701888, 17927168),
-    3: (148877, 4096000, 1001927680, 34221056),
-    4: (59319, 3869893, 712196352, 30864128),
-    5: (32768, 4173281, 635446784, 31004672),
-    6: (17576, 3869893, 518104832, 27482624),
-    7: (12167, 4251528, 518910208, 29377024),
+    1: (3944312, 4019679, 1357642752, 23140864),
+    2: (493039, 4019679, 1691100160, 74485248),
+    3: (148877, 4096000, 1002067712, 34063872),
+    4: (59319, 3869893, 711957760, 31111680),
+    5: (32768, 4173281, 672320256, 32468992),
+    6: (17576, 3869893, 518241280, 27286528),
+    7: (12167, 4251528, 519014912, 30337024),
     8: (8000, 4173281, 474237440, 29046528),
 }
 
