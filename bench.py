@@ -171,7 +171,7 @@ APPLY_F64_DRAM = {
     5: (32768, 4173281, 672320256, 32468992),
     6: (17576, 3869893, 518241280, 27286528),
     7: (12167, 4251528, 519014912, 30337024),
-    8: (8000, 4173281, 474237440, 29046528),
+    8: (8000, 4173281, 496331264, 159641344),
 }
 
 

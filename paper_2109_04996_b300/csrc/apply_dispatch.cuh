@@ -53,7 +53,10 @@ template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, b
 int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
-  auto kern = fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
+  auto kern = [] {
+    if constexpr (LinesMinBlocks<T, Q, EPB>::value) return fem_apply_lines_kernel_mb3<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
+    else return fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
+  }();
   static FemKernelCache cache;
   int &max_bps = cache.here();
   if (max_bps < 0) {

@@ -591,10 +591,9 @@ __device__ __forceinline__ void apply_group_lines(const ApplyParams<T> &prm,
 // (scalar operators over contiguous elements; the launcher picks it for FP32,
 // whose time is load latency); a separate instantiation, so that the others
 // keep their lower register count.
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
-          bool PF = false>
-__global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
-    fem_apply_lines_kernel(const LineParams<T, P, Q> lp) {
+// The kernel body, shared by the two entry points below.
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK, bool PF>
+__device__ __forceinline__ void lines_kernel_body(const LineParams<T, P, Q> &lp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *cubes = reinterpret_cast<T *>(smem_raw);
   const ApplyParams<T> &prm = lp.a;
@@ -619,6 +618,33 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
     if (fem_grid_sum<1>(v, prm.partials, prm.counter, tot) && threadIdx.x == 0)
       *prm.dot_out = tot[0];
   }
+}
+
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
+          bool PF = false>
+__global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
+    fem_apply_lines_kernel(const LineParams<T, P, Q> lp) {
+  lines_kernel_body<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>(lp);
+}
+
+// The same body held to three blocks per SM, for double words at q = 10
+// (p = 8, Gauss) with at most two elements per block (LinesMinBlocks): 80
+// registers, some spilled; 5e7 DOFs BP3 p = 8 6.21 -> 5.39 ms, 8e6 BP1 p = 8
+// 0.50 -> 0.44 ms against the best unbounded shape.  (Held to 80 registers
+// at q = 9 the same spills made p = 7 slower, 4.16 -> 4.40 ms; four elements
+// per block held to two blocks per SM spilled more and slowed down; and a
+// minimum of one block, which the entry point above leaves out, changes the
+// register allocation of the other shapes: p = 3..7 25-50 % slower.)
+template <typename T, int Q, int EPB>
+struct LinesMinBlocks {
+  static constexpr bool value = std::is_same<T, dw>::value && Q == 10 && EPB <= 2;
+};
+
+template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
+          bool PF = false>
+__global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT, 3)
+    fem_apply_lines_kernel_mb3(const LineParams<T, P, Q> lp) {
+  lines_kernel_body<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>(lp);
 }
 
 }  // namespace fem_apply

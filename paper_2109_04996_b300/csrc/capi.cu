@@ -487,9 +487,8 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   // Default launch shapes: the fastest choice (fem_apply_choices) of a
   // sweep of every choice at 8e6 DOFs on a B300 (the FP64 double-word
   // choices of BP3 at 5e7 DOFs, BP5 p = 7 at 3e7: median of four interleaved
-  // rounds; BP3 p = 8 keeps 17, within 2 % of 20, whose L2 prefetch read 1.33x
-  // the algorithmic bytes from DRAM against 17's 1.06x), per P = p + 1
-  // (index P - 2): BP3 (Gauss q = p + 2), BP5
+  // rounds; at q = 10 after the launch bound of LinesMinBlocks), per
+  // P = p + 1 (index P - 2): BP3 (Gauss q = p + 2), BP5
   // (collocated) and BP1 (Gauss mass).  FP32: the element-matrix body (7)
   // for Gauss diffusion at p = 1 (3.2x the trilinear body), the line body
   // elsewhere, often with half the default elements per block (1).  FP64:
@@ -501,11 +500,11 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   // p = 3..7, 3.2x at p = 8, 1.4x (p = 1) and 1.08x (p = 2) over the FP64
   // element matrices, 3-4x for BP5 and BP1.
   static const int kDiffF32[8] = {7, 1, 1, 0, 1, 0, 0, 1};
-  static const int kDiffF64[8] = {11, 11, 16, 8, 21, 12, 12, 17};
+  static const int kDiffF64[8] = {11, 11, 16, 8, 21, 12, 12, 15};
   static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
   static const int kCollF64[8] = {13, 9, 19, 16, 15, 21, 19, 14};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
-  static const int kMassF64[8] = {16, 16, 16, 12, 9, 9, 8, 8};
+  static const int kMassF64[8] = {16, 16, 16, 12, 9, 9, 8, 12};
   const int ip = P - 2;   // P in 2..9
   if (kind == FEM_DIFFUSION && !op->colloc) {
     op->tune_epb[FEM_F32] = kDiffF32[ip];
