@@ -87,20 +87,34 @@ def algorithmic(p, n):
     return N, E, bytes_, flops
 
 
-ELMAT_ORDERS = (1, 2)   # FP64 default body: assembled element matrices
+STENCIL_ORDERS = (1,)   # FP64 default body: the assembled 27-point stencil
+ELMAT_ORDERS = (2,)     # FP64 default body: assembled element matrices
+
+
+def stencil_bytes(N):
+    """The assembled stencil: 27 double-word coefficients per row, x and y."""
+    return 216 * N + 16 * N
+
+
+def elmat_bytes(N, E, P3):
+    return 16 * N + 4 * E * P3 + 8 * E * P3 * (P3 + 1) // 2
 
 
 def body_algorithmic(p, n):
     """Per FP64 BP3 apply with the default body: bytes that must move and
     flops it executes (FMA = 2).  p >= 3, sum factorization: algorithmic().
-    p = 1, 2, element matrices: 16N (x, y) + 4 E P^3 (indices) + 8 E P^3
+    p = 2, element matrices: 16N (x, y) + 4 E P^3 (indices) + 8 E P^3
     (P^3 + 1) / 2 (the packed upper triangle of K_e), and 2 (P^3)^2 flops
     per element for y_e = K_e x_e (each off-diagonal entry used twice) plus
-    2 P^3 for x.y."""
+    2 P^3 for x.y.  p = 1, the assembled stencil of a lattice mesh: 216N
+    (27 coefficients a row) + 16N (x, y), 2 * 27 + 2 flops a row."""
     N, E, by, fl = algorithmic(p, n)
-    if p in ELMAT_ORDERS:
+    if p in STENCIL_ORDERS:
+        by = stencil_bytes(N)
+        fl = N * (2 * 27 + 2)
+    elif p in ELMAT_ORDERS:
         P3 = (p + 1) ** 3
-        by = 16 * N + 4 * E * P3 + 8 * E * P3 * (P3 + 1) // 2
+        by = elmat_bytes(N, E, P3)
         fl = E * (2 * P3 * P3 + 2 * P3)
     return N, E, by, fl
 
@@ -159,19 +173,20 @@ def measured_peaks():
 # DRAM bytes of one FP64 BP3 apply per order, from one ncu capture
 # (dram__bytes_read.sum, dram__bytes_write.sum) of `bench.py --profile
 # BP3:<p>:f64 --dofs 4e6` on a B300: (E, N, read, write) of the captured mesh,
-# with the default (double-word) body.  The ratio to that body's algorithmic bytes
+# with the default (double-word) body (at p = 1 both kernels of one apply:
+# the split of x and the stencil).  The ratio to that body's algorithmic bytes
 # (body_algorithmic) is steady across sizes (the bytes are qdata or element
 # matrices, indices and the two vectors, all proportional to the mesh), so
 # the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 1357642752, 23140864),
-    2: (493039, 4019679, 1691100160, 74485248),
-    3: (148877, 4096000, 1002067712, 34063872),
-    4: (59319, 3869893, 711957760, 31111680),
-    5: (32768, 4173281, 672320256, 32468992),
-    6: (17576, 3869893, 518241280, 27286528),
-    7: (12167, 4251528, 519014912, 30337024),
-    8: (8000, 4173281, 496331264, 159641344),
+    1: (3944312, 4019679, 979183360, 5579776),
+    2: (493039, 4019679, 1690231040, 74249472),
+    3: (148877, 4096000, 1001807872, 34147328),
+    4: (59319, 3869893, 712169984, 30838528),
+    5: (32768, 4173281, 674142208, 32223232),
+    6: (17576, 3869893, 518104832, 27358464),
+    7: (12167, 4251528, 518849280, 29911552),
+    8: (8000, 4173281, 495704320, 157308928),
 }
 
 
@@ -182,9 +197,10 @@ def dram_ratio(p):
         return None
     E, N, rd, wr = APPLY_F64_DRAM[p]
     P, q = p + 1, p + 2
-    if p in ELMAT_ORDERS:
-        P3 = P ** 3
-        alg = 16 * N + 4 * E * P3 + 8 * E * P3 * (P3 + 1) // 2
+    if p in STENCIL_ORDERS:
+        alg = stencil_bytes(N)
+    elif p in ELMAT_ORDERS:
+        alg = elmat_bytes(N, E, P ** 3)
     else:
         alg = 16 * N + 4 * E * P ** 3 + 48 * E * q ** 3
     return (rd + wr) / alg
@@ -903,7 +919,8 @@ def main():
         _, _, _, fl_sf = algorithmic(p, n)
         per_p.append({"p": p, "N": N, "apply_ms": t_apply * 1e3,
                       "apply_gdofs": N / t_apply / 1e9,
-                      "body": ("double-word element matrices" if p in ELMAT_ORDERS
+                      "body": ("double-word assembled 27-point stencil" if p in STENCIL_ORDERS
+                               else "double-word element matrices" if p in ELMAT_ORDERS
                                else "double-word sum factorization"),
                       "apply_hbm_gbs": by / t_apply / 1e9,
                       "operator_tflops": fl / t_apply / 1e12,
@@ -925,14 +942,15 @@ def main():
                                 " null when no capture of the current bodies exists",
                 "algorithmic_bytes": tot_bytes,
                 "achieved_note": "algorithmic bytes of one FP64 apply per order (x, y, element"
-                                 " indices, qdata -- or the packed element matrices at p = 1, 2)"
+                                 " indices, qdata -- or the packed element matrices at p = 2, the"
+                                 " stencil coefficients at p = 1)"
                                  " over the summed event-timed apply durations",
                 "sum_factorized_orders_frac": (sf_bytes / sf_time / 1e9 / hbm_peak
                                                if sf_time > 0 else None),
                 "operator_tflops": tot_exec / tot_time / 1e12,
                 "sum_factorization_flops_tflops": tot_flop / tot_time / 1e12,
                 "kernel": "FP64-accurate fused apply in double-word arithmetic on the FP32 pipe"
-                          " (element-matrix body p=1,2, line body p>=3), all orders",
+                          " (assembled stencil p=1, element-matrix body p=2, line body p>=3), all orders",
                 "peak_source": "HBM copy bandwidth of measured (MEASURED_PEAKS.json)"}
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -234,7 +234,13 @@ fem_status fem_op_rhs(fem_op *op, int which, double *b);
  * bit for bit, in half the issue slots), 18, 19, 20 = 15, 16, 17 with an L2
  * bulk prefetch of the next element group's qdata and node ids, 21, 22,
  * 23 = 18, 19, 20 with the pipelined gather of 12, 13, 14 (same results as
- * 15, 16, 17 up to the order of the atomic additions).  Their
+ * 15, 16, 17 up to the order of the atomic additions), 24 = the globally
+ * assembled operator of p = 1 Gauss diffusion on a lattice mesh (the
+ * n x n x n brick with lexicographic nodes and elements, E = n^3 and
+ * N = (n+1)^3, checked at operator creation): a 27-point stencil of
+ * double-word coefficients assembled from the element matrices, applied
+ * one row per thread without atomics (whole-mesh scalar applies; element
+ * lists take 11's body); the default where it exists.  Their
  * error against exact FP64 arithmetic: ~5e-14 relative l2 for random x; for
  * diffusion each element's x_e is shifted by its node-0 value first (A_e
  * annihilates constants), which keeps the smoothest fields within ~1e-12 at

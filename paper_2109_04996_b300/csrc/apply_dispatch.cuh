@@ -54,7 +54,8 @@ int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
   auto kern = [] {
-    if constexpr (LinesMinBlocks<T, Q, EPB>::value) return fem_apply_lines_kernel_mb3<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
+    constexpr int MINB = LinesMinBlocks<T, Q, EPB>::value;
+    if constexpr (MINB > 0) return fem_apply_lines_kernel_mb<MINB, T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
     else return fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
   }();
   static FemKernelCache cache;

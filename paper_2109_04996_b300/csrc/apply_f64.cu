@@ -4,6 +4,11 @@
 int fem_launch_apply_f64_shape(fem_op *op, const double *x, double *y, const int32_t *list,
                                int64_t nsel, double *dot_out, int choice, int bps,
                                const int *skip) {
+  if (choice == FEM_CHOICE_DW_STENCIL) {
+    if (!list && nsel == op->E && op->ncomp == 1 && op->d_stencil)
+      return fem_launch_apply_stencil(op, x, y, dot_out, skip);
+    choice = FEM_CHOICE_DW_ELMAT;   // element lists: the element-matrix body
+  }
   if (fem_choice_is_dw(choice))
     return fem_launch_apply_dw_shape(op, x, y, list, nsel, dot_out, choice, bps, skip);
   fem_apply::ApplyParams<double> prm;

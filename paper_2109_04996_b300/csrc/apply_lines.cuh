@@ -627,23 +627,24 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
   lines_kernel_body<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>(lp);
 }
 
-// The same body held to three blocks per SM, for double words at q = 10
-// (p = 8, Gauss) with at most two elements per block (LinesMinBlocks): 80
-// registers, some spilled; 5e7 DOFs BP3 p = 8 6.21 -> 5.39 ms, 8e6 BP1 p = 8
-// 0.50 -> 0.44 ms against the best unbounded shape.  (Held to 80 registers
+// The same body held to MINB blocks per SM (LinesMinBlocks; 0: the
+// unbounded entry point above).  Double words at q = 10 (p = 8, Gauss) with
+// at most two elements per block: three blocks, 80 registers, some spilled;
+// 5e7 DOFs BP3 p = 8 6.21 -> 5.39 ms, 8e6 BP1 p = 8 0.50 -> 0.44 ms against
+// the best unbounded shape.  (Held to 80 registers
 // at q = 9 the same spills made p = 7 slower, 4.16 -> 4.40 ms; four elements
 // per block held to two blocks per SM spilled more and slowed down; and a
 // minimum of one block, which the entry point above leaves out, changes the
 // register allocation of the other shapes: p = 3..7 25-50 % slower.)
 template <typename T, int Q, int EPB>
 struct LinesMinBlocks {
-  static constexpr bool value = std::is_same<T, dw>::value && Q == 10 && EPB <= 2;
+  static constexpr int value = (std::is_same<T, dw>::value && Q == 10 && EPB <= 2) ? 3 : 0;
 };
 
-template <typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
+template <int MINB, typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
           bool PF = false>
-__global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT, 3)
-    fem_apply_lines_kernel_mb3(const LineParams<T, P, Q> lp) {
+__global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT, MINB)
+    fem_apply_lines_kernel_mb(const LineParams<T, P, Q> lp) {
   lines_kernel_body<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>(lp);
 }
 

@@ -100,6 +100,12 @@ struct fem_op {
   double *d_kel = nullptr;
   float *d_kel32 = nullptr;
   dw *d_keldw = nullptr;          // double-word split of d_kel (choice 11)
+  // p = 1 Gauss diffusion on a lattice mesh (stencil.cu, choice 24): the
+  // assembled 27-point stencil [27][N] in double words, the split input
+  // [N], and the lattice size n (-1: not checked yet, 0: not a lattice)
+  dw *d_stencil = nullptr;
+  dw *d_xdw = nullptr;
+  int64_t lattice_n = -1;
   double *d_diag = nullptr;       // [N] scalar diagonal
   double *d_rff = nullptr;        // [M][4]
   int M = 0;
@@ -217,7 +223,8 @@ constexpr int FEM_CHOICE_DW_ELMAT = 11;
 constexpr int FEM_CHOICE_DW_PIPE = 12;   // 12, 13, 14
 constexpr int FEM_CHOICE_DW_PACKED = 15; // 15, 16, 17
 constexpr int FEM_CHOICE_DW_PF = 18;     // 18, 19, 20 (21, 22, 23: with the pipelined gather)
-constexpr int FEM_APPLY_CHOICES_MAX = 24;
+constexpr int FEM_CHOICE_DW_STENCIL = 24;
+constexpr int FEM_APPLY_CHOICES_MAX = 25;
 inline bool fem_choice_is_dw(int c) { return c >= FEM_CHOICE_DW_LINES && c < FEM_APPLY_CHOICES_MAX; }
 // Allocate and compute the trilinear body's line sums if op has none yet
 // (capi.cu); called where choice 6 is selected, outside stream capture.
@@ -225,9 +232,13 @@ int fem_ensure_qsum(fem_op *op);
 
 // Choice c is a valid launch shape of op's apply in precision prec (6
 // exists at P = 2 only; 8..11 in FP64 only).
+bool fem_op_is_lattice(fem_op *op);
 inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
+  if (c == FEM_CHOICE_DW_STENCIL)
+    return prec == FEM_F64 && fem_has_elmat(op->kind, op->colloc, op->P) && op->P == 2 &&
+           op->ncomp == 1 && op->lattice_n > 0;
   if ((c >= FEM_CHOICE_DW_LINES && c < FEM_CHOICE_DW_ELMAT) ||
-      (c >= FEM_CHOICE_DW_PIPE && c < FEM_APPLY_CHOICES_MAX))   // 8..10, 12..23
+      (c >= FEM_CHOICE_DW_PIPE && c < FEM_CHOICE_DW_STENCIL))   // 8..10, 12..23
     return prec == FEM_F64 && (op->kind == FEM_DIFFUSION || !op->colloc);
   if (c == FEM_CHOICE_DW_ELMAT) return prec == FEM_F64 && fem_has_elmat(op->kind, op->colloc, op->P);
   return c >= 0 && c < fem_apply_choices(op) && !(c == 6 && op->P != 2);
@@ -239,6 +250,9 @@ inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
 // release their FP64 qdata and element matrices after set-up; these calls
 // rebuild them.
 int fem_ensure_choice_data(fem_op *op, int prec, int choice);
+// The assembled stencil of a lattice p = 1 diffusion operator (stencil.cu).
+int fem_ensure_stencil(fem_op *op);
+int fem_launch_apply_stencil(fem_op *op, const double *x, double *y, double *dot_out, const int *skip);
 // The FP64 qdata (recomputed from the mesh if released).
 int fem_ensure_qdata64(fem_op *op);
 // ---- p-multigrid internals used by the refined flexible CG (pmg.cu)

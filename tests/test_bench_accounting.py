@@ -25,7 +25,24 @@ def packed_entries(P3):
     return [(a, b) for a in range(P3) for b in range(a, P3)]
 
 
-@pytest.mark.parametrize("p", [1, 2])
+def test_stencil_counts_match_a_brute_force_count(bench):
+    # p = 1 on a lattice: the assembled operator, 27 coefficients a row
+    n = 7
+    N, E, by, fl = bench.body_algorithmic(1, n)
+    M = n + 1
+    assert N == M ** 3 and E == n ** 3
+    # rows x neighbour slots inside the lattice: what the coefficient array
+    # holds beyond its zeros (boundary rows have fewer neighbours)
+    inside = sum(1 for i in range(M) for j in range(M) for k in range(M)
+                 for d in range(27)
+                 if 0 <= i + d % 3 - 1 < M and 0 <= j + (d // 3) % 3 - 1 < M and 0 <= k + d // 9 - 1 < M)
+    assert inside == (3 * M - 2) ** 3
+    assert inside <= 27 * N
+    assert by == 8 * 27 * N + 16 * N                  # coefficients, x, y
+    assert fl == N * (2 * 27 + 2)                     # 27 FMAs a row + x.y
+
+
+@pytest.mark.parametrize("p", [2])
 def test_element_matrix_counts_match_a_brute_force_count(bench, p):
     n = 7
     N, E, by, fl = bench.body_algorithmic(p, n)
@@ -46,11 +63,13 @@ def test_sum_factorized_orders_keep_the_general_count(bench, p):
 
 def test_traffic_ratios_are_near_the_algorithmic_bytes(bench):
     # every order has a capture of its current default body, moving 1.0-1.2x
-    # the algorithmic bytes (scattered y sectors, shared-node x re-reads)
+    # the algorithmic bytes (scattered y sectors, shared-node x re-reads, the
+    # stencil's split pass), 1.4x at p = 8 (register spills of the body held
+    # to three blocks per SM reach DRAM)
     total = 0.0
     for p in range(1, 9):
         r = bench.dram_ratio(p)
-        assert r is not None and 1.0 <= r <= 1.2, (p, r)
+        assert r is not None and 1.0 <= r <= (1.4 if p == 8 else 1.2), (p, r)
         n = fem_inputs.bp3_mesh_n(5e7, p)
         total += r * bench.body_algorithmic(p, n)[2]
     assert total > 0
