@@ -224,7 +224,12 @@ int fem_launch_apply_stencil(fem_op *op, const double *x, double *y, double *dot
   if (grid > need) grid = need;
   if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
   if (grid < 1) grid = 1;
-  fem_apply_split_kernel<<<(unsigned)grid, kThreads, 0, op->stream()>>>(x, op->d_xdw, N, skip);
+  // (a plain stream: its own, larger grid -- at the stencil's two blocks
+  // per SM it ran at a third of the copy rate)
+  int64_t gsplit = (int64_t)op->nsm * 16;
+  if (gsplit > need) gsplit = need;
+  if (gsplit < 1) gsplit = 1;
+  fem_apply_split_kernel<<<(unsigned)gsplit, kThreads, 0, op->stream()>>>(x, op->d_xdw, N, skip);
   FEM_CHECK_LAUNCH();
   StencilParams sp;
   sp.A = op->d_stencil; sp.x = op->d_xdw; sp.y = y; sp.N = N; sp.M = (int)(op->lattice_n + 1);
