@@ -958,9 +958,12 @@ def main():
             "data": "synthetic", "config": config(args, work),
             "e2e": {"value": dof_it * world / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
-            # per order: prepare + init, then 3 kernels per iteration in
-            # passes of 4 (kernels after the last iteration return at once)
-            "gpu_launches": len(ops) * (2 + 3 * 4 * ((args.iters + 3) // 4)) * args.steps,
+            # per order: prepare + init, then per iteration the apply (two
+            # kernels for the p = 1 stencil: the split of x and the stencil,
+            # one otherwise), update and direction, in passes of 4 (kernels
+            # after the last iteration return at once)
+            "gpu_launches": sum(2 + (4 if p in STENCIL_ORDERS else 3) * 4 * ((args.iters + 3) // 4)
+                                for p, _ in work) * args.steps,
             "roofline": roofline, "clocks": clocks, "per_order": per_p}
     del ops
     # the untimed single-GPU sections run at N = 1 only (a multi-rank run is
