@@ -201,7 +201,7 @@ int launch_elmat(fem_op *op, const ApplyParams<T> &prm, int bps) {
 // p = 1 only; the slab body's default elsewhere), 7 the element-matrix body
 // (Gauss diffusion at p = 1, 2); the collocated mass operator (pointwise)
 // has only the slab body.
-// Double words (FP64 operators, choices 8..11): the line body and the
+// Double words (FP64 operators, choices 8..23): the line body and the
 // element-matrix body.
 template <int P, int Q, int KIND, bool COLLOC>
 int launch_epb_dw(fem_op *op, const ApplyParams<dw> &prm, int choice, int bps) {

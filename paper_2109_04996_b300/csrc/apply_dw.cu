@@ -1,4 +1,4 @@
-// Double-word instantiations of the fused apply (launch choices 8..11 of an
+// Double-word instantiations of the fused apply (launch choices 8..23 of an
 // FP64 operator; see dw.cuh): the gathered FP64 x values are split into
 // double words, the qdata (or element matrices) are read from the
 // operator's double-word copy, the contractions and the pointwise products

@@ -213,7 +213,7 @@ int ensure_keldw(fem_op *op) {
 
 int fem_ensure_qsum(fem_op *op) { return ensure_qsum(op); }
 
-// The double-word split of the qdata (choices 8..10), made when one of
+// The double-word split of the qdata (line-body choices), made when one of
 // those bodies is first selected.
 static int ensure_qdw(fem_op *op) {
   if (op->d_qdw) return FEM_OK;

@@ -86,7 +86,7 @@ struct fem_op {
   float *d_B32 = nullptr, *d_Dq32 = nullptr;
   double *d_qdata = nullptr;      // [E][nd][Q^3]
   float *d_qdata32 = nullptr;     // FP32 copy (prec == FEM_F32)
-  dw *d_qdw = nullptr;            // double-word split (choices 8..10), made
+  dw *d_qdw = nullptr;            // double-word split (line-body choices 8..23), made
                                   // when one of them is first selected
   // trilinear Gauss diffusion only (P = 2), made when the trilinear body is
   // first selected (fem_ensure_qsum): line sums of the diagonal qdata
@@ -170,7 +170,7 @@ int fem_launch_apply_f64_shape(fem_op *op, const double *x, double *y, const int
 int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32_t *list,
                                int64_t nsel, double *dot_out, int choice, int bps,
                                const int *skip = nullptr);
-// the double-word bodies (choices 8..11) of the FP64 apply (apply_dw.cu)
+// the double-word bodies (choices 8..23) of the FP64 apply (apply_dw.cu)
 int fem_launch_apply_dw_shape(fem_op *op, const double *x, double *y, const int32_t *list,
                               int64_t nsel, double *dot_out, int choice, int bps,
                               const int *skip = nullptr);
@@ -231,7 +231,7 @@ inline bool fem_choice_is_dw(int c) { return c >= FEM_CHOICE_DW_LINES && c < FEM
 int fem_ensure_qsum(fem_op *op);
 
 // Choice c is a valid launch shape of op's apply in precision prec (6
-// exists at P = 2 only; 8..11 in FP64 only).
+// exists at P = 2 only; 8..24 in FP64 only).
 bool fem_op_is_lattice(fem_op *op);
 inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
   if (c == FEM_CHOICE_DW_STENCIL)
