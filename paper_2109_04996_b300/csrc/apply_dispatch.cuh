@@ -54,7 +54,7 @@ int launch_lines_kernel(fem_op *op, const LineParams<T, P, Q> &lp, int bps) {
   constexpr int NT = ApplyShape<Q, EPB>::NT;
   constexpr size_t smem = lines_smem_bytes<T, Q, EPB>();
   auto kern = [] {
-    constexpr int MINB = LinesMinBlocks<T, Q, EPB>::value;
+    constexpr int MINB = LinesMinBlocks<T, Q, EPB, PIPE, KIND, PK, PF>::value;
     if constexpr (MINB > 0) return fem_apply_lines_kernel_mb<MINB, T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
     else return fem_apply_lines_kernel<T, P, Q, COLLOC, EPB, PIPE, KIND, PK, PF>;
   }();

@@ -628,17 +628,32 @@ __global__ void __launch_bounds__(ApplyShape<Q, EPB>::NT)
 }
 
 // The same body held to MINB blocks per SM (LinesMinBlocks; 0: the
-// unbounded entry point above).  Double words at q = 10 (p = 8, Gauss) with
-// at most two elements per block: three blocks, 80 registers, some spilled;
-// 5e7 DOFs BP3 p = 8 6.21 -> 5.39 ms, 8e6 BP1 p = 8 0.50 -> 0.44 ms against
-// the best unbounded shape.  (Held to 80 registers
-// at q = 9 the same spills made p = 7 slower, 4.16 -> 4.40 ms; four elements
-// per block held to two blocks per SM spilled more and slowed down; and a
-// minimum of one block, which the entry point above leaves out, changes the
-// register allocation of the other shapes: p = 3..7 25-50 % slower.)
-template <typename T, int Q, int EPB>
+// unbounded entry point above), for the shapes where that measured faster
+// (5e7 DOFs, the best bounded against the best unbounded shape):
+//   q = 10 (p = 8, Gauss), at most two elements per block: three blocks,
+//     80 registers, some spilled; BP3 p = 8 6.21 -> 5.39 ms (BP1 p = 8 at
+//     8e6: 0.50 -> 0.44 ms);
+//   double-word diffusion with the pipelined gather, packed contractions and
+//   the L2 prefetch at q = 7 (5 elements per block) and q = 8 (4): two
+//     blocks; BP3 p = 5 4.44 -> 4.33 ms, p = 6 4.19 -> 4.04 ms, BP5 p = 7
+//     (q = 8, collocated) 1.26 -> 1.19 ms;
+//   the pipelined gather alone at q = 9 (3 elements per block): two blocks;
+//     BP3 p = 7 4.15 -> 4.10 ms (BP5 p = 8 at 8e6: 0.40 -> 0.36 ms).
+// The other shapes lost 10-60 % under the same bounds, and so did q = 9
+// held to three blocks (4.16 -> 4.40 ms) and four elements per block at
+// q = 10 held to two; a minimum of one block, which the entry point above
+// leaves out, changes the register allocation of every shape: p = 3..7
+// 25-50 % slower.
+template <typename T, int Q, int EPB, bool PIPE = false, int KIND = FEM_DIFFUSION, bool PK = false,
+          bool PF = false>
 struct LinesMinBlocks {
-  static constexpr int value = (std::is_same<T, dw>::value && Q == 10 && EPB <= 2) ? 3 : 0;
+  static constexpr bool DW = std::is_same<T, dw>::value, DIFF = KIND == FEM_DIFFUSION;
+  static constexpr int value =
+      !DW ? 0
+      : (Q == 10 && EPB <= 2) ? 3
+      : (DIFF && PIPE && PK && PF && ((Q == 7 && EPB == 5) || (Q == 8 && EPB == 4))) ? 2
+      : (DIFF && PIPE && !PK && !PF && Q == 9 && EPB == 3) ? 2
+      : 0;
 };
 
 template <int MINB, typename T, int P, int Q, bool COLLOC, int EPB, bool PIPE, int KIND, bool PK = false,
