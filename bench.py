@@ -179,14 +179,14 @@ def measured_peaks():
 # matrices, indices and the two vectors, all proportional to the mesh), so
 # the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 979183360, 5579776),
-    2: (493039, 4019679, 1690231040, 74249472),
-    3: (148877, 4096000, 1001807872, 34147328),
-    4: (59319, 3869893, 712169984, 30838528),
-    5: (32768, 4173281, 674142208, 32223232),
-    6: (17576, 3869893, 518104832, 27358464),
-    7: (12167, 4251528, 518849280, 29911552),
-    8: (8000, 4173281, 495704320, 157308928),
+    1: (3944312, 4019679, 978895872, 5820928),
+    2: (493039, 4019679, 1691048704, 74798336),
+    3: (148877, 4096000, 1001912064, 34144256),
+    4: (59319, 3869893, 712047360, 30795520),
+    5: (32768, 4173281, 672312576, 32482048),
+    6: (17576, 3869893, 621730048, 29718016),
+    7: (12167, 4251528, 518859520, 29872128),
+    8: (8000, 4173281, 495895296, 157352960),
 }
 
 

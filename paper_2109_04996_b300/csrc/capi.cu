@@ -510,13 +510,19 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   static const int kCollF64[8] = {13, 9, 19, 16, 15, 21, 21, 12};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
   static const int kMassF64[8] = {16, 16, 16, 12, 9, 9, 8, 12};
+  // Vector diffusion (BP4, BP6): the pipelined gather serves scalar
+  // operators only, so their FP64 defaults come from their own sweep (BP4 and
+  // BP6 at about 4e6 nodes per component, BP6 p = 7 at 2.95e7).
+  static const int kDiffVecF64[8] = {11, 11, 19, 8, 8, 8, 8, 8};
+  static const int kCollVecF64[8] = {9, 9, 19, 16, 15, 16, 19, 15};
   const int ip = P - 2;   // P in 2..9
+  const bool vec = ncomp > 1;
   if (kind == FEM_DIFFUSION && !op->colloc) {
     op->tune_epb[FEM_F32] = kDiffF32[ip];
-    op->tune_epb[FEM_F64] = kDiffF64[ip];
+    op->tune_epb[FEM_F64] = vec ? kDiffVecF64[ip] : kDiffF64[ip];
   } else if (kind == FEM_DIFFUSION) {
     op->tune_epb[FEM_F32] = kCollF32[ip];
-    op->tune_epb[FEM_F64] = kCollF64[ip];
+    op->tune_epb[FEM_F64] = vec ? kCollVecF64[ip] : kCollF64[ip];
   } else if (!op->colloc) {
     op->tune_epb[FEM_F32] = kMassF32[ip];
     op->tune_epb[FEM_F64] = kMassF64[ip];

@@ -64,12 +64,13 @@ def test_sum_factorized_orders_keep_the_general_count(bench, p):
 def test_traffic_ratios_are_near_the_algorithmic_bytes(bench):
     # every order has a capture of its current default body, moving 1.0-1.2x
     # the algorithmic bytes (scattered y sectors, shared-node x re-reads, the
-    # stencil's split pass), 1.4x at p = 8 (register spills of the body held
-    # to three blocks per SM reach DRAM)
+    # stencil's split pass), up to 1.4x where the body prefetches the next
+    # group's qdata into L2 and part of it is evicted before use (p = 5, 6)
+    # or spills registers to DRAM under its launch bound (p = 8)
     total = 0.0
     for p in range(1, 9):
         r = bench.dram_ratio(p)
-        assert r is not None and 1.0 <= r <= (1.4 if p == 8 else 1.2), (p, r)
+        assert r is not None and 1.0 <= r <= (1.4 if p in (5, 6, 8) else 1.2), (p, r)
         n = fem_inputs.bp3_mesh_n(5e7, p)
         total += r * bench.body_algorithmic(p, n)[2]
     assert total > 0
