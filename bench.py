@@ -92,8 +92,9 @@ ELMAT_ORDERS = (2,)     # FP64 default body: assembled element matrices
 
 
 def stencil_bytes(N):
-    """The assembled stencil: 27 double-word coefficients per row, x and y."""
-    return 216 * N + 16 * N
+    """The assembled stencil: 26 double-word off-diagonal coefficients per
+    row (the diagonal is implied by the zero row sums), x and y."""
+    return 208 * N + 16 * N
 
 
 def elmat_bytes(N, E, P3):
@@ -106,12 +107,13 @@ def body_algorithmic(p, n):
     p = 2, element matrices: 16N (x, y) + 4 E P^3 (indices) + 8 E P^3
     (P^3 + 1) / 2 (the packed upper triangle of K_e), and 2 (P^3)^2 flops
     per element for y_e = K_e x_e (each off-diagonal entry used twice) plus
-    2 P^3 for x.y.  p = 1, the assembled stencil of a lattice mesh: 216N
-    (27 coefficients a row) + 16N (x, y), 2 * 27 + 2 flops a row."""
+    2 P^3 for x.y.  p = 1, the assembled stencil of a lattice mesh: 208N
+    (26 off-diagonal coefficients a row) + 16N (x, y), 26 differences and
+    26 FMAs plus x.y: 3 * 26 + 2 flops a row."""
     N, E, by, fl = algorithmic(p, n)
     if p in STENCIL_ORDERS:
         by = stencil_bytes(N)
-        fl = N * (2 * 27 + 2)
+        fl = N * (3 * 26 + 2)
     elif p in ELMAT_ORDERS:
         P3 = (p + 1) ** 3
         by = elmat_bytes(N, E, P3)
@@ -179,7 +181,7 @@ def measured_peaks():
 # matrices, indices and the two vectors, all proportional to the mesh), so
 # the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 978895872, 5820928),
+    1: (3944312, 4019679, 945578752, 5198848),
     2: (493039, 4019679, 1691048704, 74798336),
     3: (148877, 4096000, 1001912064, 34144256),
     4: (59319, 3869893, 712047360, 30795520),
