@@ -5,6 +5,11 @@
 int fem_launch_apply_f32_shape(fem_op *op, const float *x, float *y, const int32_t *list,
                                int64_t nsel, double *dot_out, int choice, int bps,
                                const int *skip) {
+  if (choice == FEM_CHOICE_DW_STENCIL) {
+    if (!list && nsel == op->E && op->ncomp == 1 && op->d_stencil32)
+      return fem_launch_apply_stencil_f32(op, x, y, dot_out, skip);
+    choice = 7;   // element lists: the element-matrix body
+  }
   if (!op->d_qdata32) {
     fem_set_error("apply_f32: operator was not created with FEM_F32");
     return FEM_EINVAL;

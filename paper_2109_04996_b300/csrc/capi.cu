@@ -231,8 +231,8 @@ int fem_ensure_choice_data(fem_op *op, int prec, int choice) {
   if (choice == FEM_CHOICE_DW_ELMAT) return ensure_keldw(op);
   if (choice == FEM_CHOICE_DW_STENCIL) {
     // the stencil, and the element matrices for element-list applies
-    int rc = ensure_keldw(op);
-    return rc ? rc : fem_ensure_stencil(op);
+    int rc = prec == FEM_F64 ? ensure_keldw(op) : ensure_kel64(op);
+    return rc ? rc : fem_ensure_stencil(op, prec);
   }
   if (fem_choice_is_dw(choice)) return ensure_qdw(op);
   if (prec == FEM_F64) return choice == 7 ? ensure_kel64(op) : ensure_qdata64(op);
@@ -582,9 +582,10 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   }
   // p = 1 Gauss diffusion on a lattice mesh: the assembled stencil (24)
   // replaces the element matrices as the FP64 default
-  if (fem_has_elmat(kind, op->colloc, P) && P == 2 && op->ncomp == 1 && fem_op_is_lattice(op) &&
-      op->tune_epb[FEM_F64] == FEM_CHOICE_DW_ELMAT)
-    op->tune_epb[FEM_F64] = FEM_CHOICE_DW_STENCIL;
+  if (fem_has_elmat(kind, op->colloc, P) && P == 2 && op->ncomp == 1 && fem_op_is_lattice(op)) {
+    if (op->tune_epb[FEM_F64] == FEM_CHOICE_DW_ELMAT) op->tune_epb[FEM_F64] = FEM_CHOICE_DW_STENCIL;
+    if (prec == FEM_F32 && op->tune_epb[FEM_F32] == 7) op->tune_epb[FEM_F32] = FEM_CHOICE_DW_STENCIL;
+  }
   // the data of the default launch choices (trilinear line sums, split
   // qdata or element matrices)
   if ((rc = fem_ensure_choice_data(op, FEM_F64, op->tune_epb[FEM_F64])) ||
@@ -625,7 +626,7 @@ extern "C" fem_status fem_op_destroy(fem_op *op) {
   cudaFree(op->d_qdata); cudaFree(op->d_qdata32); cudaFree(op->d_diag); cudaFree(op->d_rff);
   cudaFree(op->d_qsum); cudaFree(op->d_qsum32);
   cudaFree(op->d_kel); cudaFree(op->d_kel32); cudaFree(op->d_keldw); cudaFree(op->d_qdw);
-  cudaFree(op->d_stencil); cudaFree(op->d_xdw);
+  cudaFree(op->d_stencil); cudaFree(op->d_xdw); cudaFree(op->d_stencil32);
   cudaFree(op->d_partials); cudaFree(op->d_counter);
   delete op;
   return FEM_OK;

@@ -105,6 +105,7 @@ struct fem_op {
   // [N], and the lattice size n (-1: not checked yet, 0: not a lattice)
   dw *d_stencil = nullptr;
   dw *d_xdw = nullptr;
+  float *d_stencil32 = nullptr;   // the same in FP32 (FP32 operators)
   int64_t lattice_n = -1;
   double *d_diag = nullptr;       // [N] scalar diagonal
   double *d_rff = nullptr;        // [M][4]
@@ -185,7 +186,9 @@ int fem_launch_apply_dw_shape(fem_op *op, const double *x, double *y, const int3
 // group's x gather carried one group ahead (scalar operators over whole
 // meshes; element lists and vector operators take 8..10's body), 15..17 the
 // line-based body with its even and odd contractions carried as packed
-// f32x2 pairs.
+// f32x2 pairs, 18..23 those with an L2 prefetch of the next group's qdata;
+// 24 (FP64 and FP32) the assembled stencil of p = 1 Gauss diffusion on a
+// lattice mesh (stencil.cu).
 inline bool fem_has_elmat(int kind, bool colloc, int P) {
   return kind == FEM_DIFFUSION && !colloc && (P == 2 || P == 3);
 }
@@ -234,9 +237,9 @@ int fem_ensure_qsum(fem_op *op);
 // exists at P = 2 only; 8..24 in FP64 only).
 bool fem_op_is_lattice(fem_op *op);
 inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
-  if (c == FEM_CHOICE_DW_STENCIL)
-    return prec == FEM_F64 && fem_has_elmat(op->kind, op->colloc, op->P) && op->P == 2 &&
-           op->ncomp == 1 && op->lattice_n > 0;
+  if (c == FEM_CHOICE_DW_STENCIL)   // FP64 (double words) and FP32
+    return (prec == FEM_F64 || op->prec == FEM_F32) && fem_has_elmat(op->kind, op->colloc, op->P) &&
+           op->P == 2 && op->ncomp == 1 && op->lattice_n > 0;
   if ((c >= FEM_CHOICE_DW_LINES && c < FEM_CHOICE_DW_ELMAT) ||
       (c >= FEM_CHOICE_DW_PIPE && c < FEM_CHOICE_DW_STENCIL))   // 8..10, 12..23
     return prec == FEM_F64 && (op->kind == FEM_DIFFUSION || !op->colloc);
@@ -251,8 +254,9 @@ inline bool fem_apply_choice_valid(const fem_op *op, int prec, int c) {
 // rebuild them.
 int fem_ensure_choice_data(fem_op *op, int prec, int choice);
 // The assembled stencil of a lattice p = 1 diffusion operator (stencil.cu).
-int fem_ensure_stencil(fem_op *op);
+int fem_ensure_stencil(fem_op *op, int prec);
 int fem_launch_apply_stencil(fem_op *op, const double *x, double *y, double *dot_out, const int *skip);
+int fem_launch_apply_stencil_f32(fem_op *op, const float *x, float *y, double *dot_out, const int *skip);
 // The FP64 qdata (recomputed from the mesh if released).
 int fem_ensure_qdata64(fem_op *op);
 // ---- p-multigrid internals used by the refined flexible CG (pmg.cu)

@@ -35,7 +35,9 @@
 // the element-matrix body (choice 11), which the selection also prepares.
 #include <math.h>
 
-#include "fem_internal.h"
+#include <type_traits>
+
+#include "apply_kernel.cuh"
 
 namespace {
 
@@ -62,7 +64,8 @@ __global__ void lattice_check_kernel(const int32_t *en, int64_t E, int64_t n, un
 // Row i of the stencil from the FP64 element matrices (row-packed upper
 // triangle, entry-major [36][E]): the 26 off-diagonal slots, slot s of
 // offset d at s' = s - (s > 13) with s = (dx+1) + 3 (dy+1) + 9 (dz+1).
-__global__ void stencil_assemble_kernel(const double *kel, int64_t E, int64_t n, dw *A) {
+template <typename T>
+__global__ void stencil_assemble_kernel(const double *kel, int64_t E, int64_t n, T *A) {
   const int64_t M = n + 1, N = M * M * M;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -85,8 +88,11 @@ __global__ void stencil_assemble_kernel(const double *kel, int64_t E, int64_t n,
       }
     }
 #pragma unroll
-    for (int s = 0; s < 27; s++)
-      if (s != 13) A[(int64_t)(s - (s > 13)) * N + i] = dw_from_double(acc[s]);
+    for (int s = 0; s < 27; s++) {
+      if (s == 13) continue;
+      if constexpr (std::is_same<T, dw>::value) A[(int64_t)(s - (s > 13)) * N + i] = dw_from_double(acc[s]);
+      else A[(int64_t)(s - (s > 13)) * N + i] = (T)acc[s];
+    }
   }
 }
 
@@ -162,6 +168,61 @@ __global__ void __launch_bounds__(kThreads, 3) fem_apply_stencil27_kernel(const 
   }
 }
 
+// The same stencil in FP32 (FP32 operators, e.g. the coarse levels of an
+// FP32 p-multigrid V-cycle): FP32 coefficients (104 bytes a row) and x, no
+// split pass, x^T y by the FP32 bodies' compensated accumulation.
+struct StencilParams32 {
+  const float *A;      // [26][N]
+  const float *x;
+  float *y;            // accumulated
+  int64_t N;
+  int M;
+  double *partials;
+  unsigned *counter;
+  double *dot_out;
+  const int *skip;
+};
+
+__global__ void __launch_bounds__(kThreads, 3) fem_apply_stencil27_f32_kernel(const StencilParams32 sp) {
+  if (sp.skip && *(volatile const int *)sp.skip) return;
+  const int M = sp.M;
+  const int64_t M2 = (int64_t)M * M;
+  fem_apply::DotAcc<float> dl;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sp.N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned u = (unsigned)i, um = (unsigned)M;
+    const unsigned ix = u % um, t = u / um, iy = t % um, iz = t / um;
+    float a[26];
+#pragma unroll
+    for (int s = 0; s < 26; s++) a[s] = __ldcs(sp.A + (int64_t)s * sp.N + i);
+    asm volatile("" ::: "memory");
+    const float xi = sp.x[i];
+    float acc = 0.0f;
+#pragma unroll
+    for (int dz = -1; dz <= 1; dz++) {
+#pragma unroll
+      for (int dy = -1; dy <= 1; dy++) {
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+          const int s = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+          if (s == 13) continue;
+          const bool in = (dx >= 0 || ix > 0) && (dx <= 0 || ix + 1 < um) && (dy >= 0 || iy > 0) &&
+                          (dy <= 0 || iy + 1 < um) && (dz >= 0 || iz > 0) && (dz <= 0 || iz + 1 < um);
+          const int64_t j = in ? i + dx + (int64_t)M * dy + M2 * dz : i;
+          acc = fmaf(a[s - (s > 13)], sp.x[j] - xi, acc);
+        }
+      }
+    }
+    dl.add(acc, xi);
+    sp.y[i] += acc;
+  }
+  if (sp.dot_out) {
+    double v[1] = {dl.get()};
+    __shared__ double tot[1];
+    if (fem_grid_sum<1>(v, sp.partials, sp.counter, tot) && threadIdx.x == 0) *sp.dot_out = tot[0];
+  }
+}
+
 }  // namespace
 
 // Is op's mesh a lattice (see lattice_check_kernel)?  Checked once per
@@ -189,9 +250,27 @@ bool fem_op_is_lattice(fem_op *op) {
   return op->lattice_n > 0;
 }
 
-// The stencil coefficients and the split-input buffer (needs the FP64
-// element matrices, which the caller makes first).
-int fem_ensure_stencil(fem_op *op) {
+// The stencil coefficients and, in FP64, the split-input buffer (needs the
+// FP64 element matrices, which the caller makes first).
+int fem_ensure_stencil(fem_op *op, int prec) {
+  if (prec == FEM_F32) {
+    if (op->d_stencil32) return FEM_OK;
+    if (!fem_op_is_lattice(op) || !op->d_kel) {
+      fem_set_error("apply: the assembled stencil (choice 24) needs p = 1 Gauss diffusion on a lattice mesh");
+      return FEM_EINVAL;
+    }
+    if (cudaMalloc(&op->d_stencil32, sizeof(float) * 26 * (size_t)op->N) != cudaSuccess) {
+      cudaGetLastError();
+      op->d_stencil32 = nullptr;
+      fem_set_error("apply: device allocation of the stencil failed");
+      return FEM_ENOMEM;
+    }
+    op->bytes += (int64_t)(sizeof(float) * 26 * (size_t)op->N);
+    stencil_assemble_kernel<float><<<op->nsm * 8, kThreads, 0, op->stream()>>>(op->d_kel, op->E, op->lattice_n,
+                                                                                op->d_stencil32);
+    FEM_CHECK_LAUNCH();
+    return FEM_OK;
+  }
   if (op->d_stencil && op->d_xdw) return FEM_OK;
   if (!fem_op_is_lattice(op) || !op->d_kel) {
     fem_set_error("apply: the assembled stencil (choice 24) needs p = 1 Gauss diffusion on a lattice mesh");
@@ -206,8 +285,8 @@ int fem_ensure_stencil(fem_op *op) {
       return FEM_ENOMEM;
     }
     op->bytes += (int64_t)(sizeof(dw) * 26 * (size_t)N);
-    stencil_assemble_kernel<<<op->nsm * 8, kThreads, 0, op->stream()>>>(op->d_kel, op->E, op->lattice_n,
-                                                                         op->d_stencil);
+    stencil_assemble_kernel<dw><<<op->nsm * 8, kThreads, 0, op->stream()>>>(op->d_kel, op->E, op->lattice_n,
+                                                                             op->d_stencil);
     FEM_CHECK_LAUNCH();
   }
   if (!op->d_xdw) {
@@ -250,6 +329,31 @@ int fem_launch_apply_stencil(fem_op *op, const double *x, double *y, double *dot
   sp.A = op->d_stencil; sp.x = op->d_xdw; sp.y = y; sp.N = N; sp.M = (int)(op->lattice_n + 1);
   sp.partials = op->d_partials; sp.counter = op->d_counter; sp.dot_out = dot_out; sp.skip = skip;
   fem_apply_stencil27_kernel<<<(unsigned)grid, kThreads, 0, op->stream()>>>(sp);
+  FEM_CHECK_LAUNCH();
+  return FEM_OK;
+}
+
+int fem_launch_apply_stencil_f32(fem_op *op, const float *x, float *y, double *dot_out, const int *skip) {
+  if (!op->d_stencil32) {
+    fem_set_error("apply_f32: the assembled stencil is not set up");
+    return FEM_EINVAL;
+  }
+  static FemKernelCache cache;
+  int &per_sm = cache.here();
+  if (per_sm < 0) {
+    int b = 0;
+    FEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fem_apply_stencil27_f32_kernel, kThreads, 0));
+    per_sm = b < 1 ? 1 : b;
+  }
+  const int64_t N = op->N;
+  int64_t grid = (int64_t)op->nsm * per_sm, need = (N + kThreads - 1) / kThreads;
+  if (grid > need) grid = need;
+  if (grid > FEM_MAX_BLOCKS) grid = FEM_MAX_BLOCKS;
+  if (grid < 1) grid = 1;
+  StencilParams32 sp;
+  sp.A = op->d_stencil32; sp.x = x; sp.y = y; sp.N = N; sp.M = (int)(op->lattice_n + 1);
+  sp.partials = op->d_partials; sp.counter = op->d_counter; sp.dot_out = dot_out; sp.skip = skip;
+  fem_apply_stencil27_f32_kernel<<<(unsigned)grid, kThreads, 0, op->stream()>>>(sp);
   FEM_CHECK_LAUNCH();
   return FEM_OK;
 }

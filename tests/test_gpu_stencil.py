@@ -103,3 +103,51 @@ def test_stencil_cg_matches_oracle_pcg(use_graph):
     inner = m["dirichlet"] == 0
     res = np.where(inner, b - orc.apply(x.cpu().numpy()), 0.0)
     assert np.linalg.norm(res) <= 2e-10 * np.linalg.norm(b)
+
+
+def make32(n, seed=3):
+    m = fem_inputs.box_mesh(n, 1, perturb=0.1, seed=seed)
+    gm = fem.Mesh(m)
+    op = fem.Operator(gm, fem.DIFFUSION, fem.GAUSS, 3, prec=fem.F32)
+    orc = oracle.Operator(m, oracle.DIFFUSION, oracle.GAUSS, 3)
+    return m, gm, op, orc
+
+
+@pytest.mark.parametrize("n", [2, 7, 12])
+def test_stencil_f32_matches_oracle_and_element_matrices(n):
+    # the FP32 stencil: the FP32 bar (1e-5), its own default, deterministic
+    m, gm, op, orc = make32(n, seed=20 + n)
+    for xv in fields(m, seed=n):
+        ref = orc.apply(xv)
+        x = torch.from_numpy(xv).cuda().float()
+        y_def = op.apply_f32(x)
+        op.set_launch_shape(fem.F32, STENCIL)
+        y24 = op.apply_f32(x)
+        y24b = op.apply_f32(x)
+        op.set_launch_shape(fem.F32, 7)
+        y7 = op.apply_f32(x)
+        op.set_launch_shape(fem.F32, STENCIL)
+        assert torch.equal(y24, y24b) and torch.equal(y_def, y24)
+        assert rel(y24.double().cpu().numpy(), ref) <= 1e-5
+        assert rel(y24.double().cpu().numpy(), y7.double().cpu().numpy()) <= 1e-5
+    # the FP64 apply of the same operator keeps its own (double-word) stencil
+    xv = fields(m, seed=1)[0]
+    assert rel(op.apply(torch.from_numpy(xv).cuda()).cpu().numpy(), orc.apply(xv)) <= 1e-12
+
+
+def test_stencil_f32_refused_on_fp64_operator():
+    m, gm, op, orc = make(3)
+    with pytest.raises(fem.FemError):
+        op.set_launch_shape(fem.F32, STENCIL)
+
+
+def test_stencil_refined_solve():
+    # FP32 inner CG on the FP32 stencil, FP64 residuals on the double-word one
+    m, gm, op, orc = make32(9, seed=8)
+    b = fem_inputs.rhs_uniform(m["N"], m["dirichlet"], seed=5)
+    x = torch.zeros(m["N"], dtype=torch.float64, device="cuda")
+    st = op.solve_refined(torch.from_numpy(b).cuda(), x, rtol=1e-10, inner_rtol=0.1)
+    assert st["status"] == "FEM_OK"
+    inner = m["dirichlet"] == 0
+    res = np.where(inner, b - orc.apply(x.cpu().numpy()), 0.0)
+    assert np.linalg.norm(res) <= 2e-10 * np.linalg.norm(b)
