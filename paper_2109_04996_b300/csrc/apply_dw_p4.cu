@@ -1,4 +1,6 @@
 // Double-word apply bodies of order P = 4 (see apply_dw.cu).
+// the double-word sums by ordered Fast2Sum (dw.cuh: faster at this order)
+#define FEM_DW_ADD_ORDERED 1
 #include "apply_dispatch.cuh"
 
 template <int P>

@@ -43,9 +43,28 @@ __device__ __forceinline__ void dw_two_sum(float a, float b, float &s, float &e)
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// FEM_DW_ADD_ORDERED (set per translation unit before this header): the
+// exact error of s = a.h + b.h by Fast2Sum on the operands ordered by
+// magnitude (Dekker 1971) instead of TwoSum -- the same e, hence the same
+// result bit for bit, from 3 FP32 additions instead of 6 plus a compare and
+// two selects on the ALU pipe.  Measured on the headline sweep (5e7 DOFs,
+// ms): p = 3, 5, 6, 7, 8 faster (5.32 -> 5.18, 4.34 -> 4.30, 4.05 -> 3.95,
+// 4.11 -> 3.99, 5.40 -> 5.32), p = 1, 2, 4 slower (the stencil 2.27 ->
+// 2.41, the element matrices 5.03 -> 5.10, 4.93 -> 4.96), so the orders'
+// translation units choose.
+#ifndef FEM_DW_ADD_ORDERED
+#define FEM_DW_ADD_ORDERED 0
+#endif
 __device__ __forceinline__ dw operator+(dw a, dw b) {
+#if FEM_DW_ADD_ORDERED
+  const float s = __fadd_rn(a.h, b.h);
+  const bool big = fabsf(a.h) >= fabsf(b.h);
+  const float x = big ? a.h : b.h, y = big ? b.h : a.h;
+  const float e = __fsub_rn(y, __fsub_rn(s, x));
+#else
   float s, e;
   dw_two_sum(a.h, b.h, s, e);
+#endif
   return dw(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
 }
 __device__ __forceinline__ dw operator-(dw a) { return dw(-a.h, -a.l); }
