@@ -507,7 +507,7 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   static const int kDiffF32[8] = {7, 1, 1, 0, 1, 0, 0, 1};
   static const int kDiffF64[8] = {11, 11, 16, 8, 21, 21, 12, 15};
   static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
-  static const int kCollF64[8] = {13, 9, 19, 16, 15, 21, 21, 12};
+  static const int kCollF64[8] = {13, 9, 22, 16, 15, 21, 21, 12};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
   static const int kMassF64[8] = {16, 16, 16, 12, 9, 9, 8, 12};
   // Vector diffusion (BP4, BP6): the pipelined gather serves scalar
