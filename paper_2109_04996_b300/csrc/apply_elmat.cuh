@@ -9,7 +9,7 @@
 // the scatter-add.  The paper keeps full assembly for first and second
 // order and partial assembly for high order (section "Miniapps": Laghos'
 // full and partial assembly options), and on B300 the FP64 apply agrees:
-// FP64 runs at 1/64 of the FP32 rate and bounds the partially assembled
+// FP64 runs at about 1/73 of the FP32 rate and bounds the partially assembled
 // apply, while K_e costs (P^3)^2 FMAs per element (64 at p = 1, 729 at
 // p = 2) against about 370 and 1500 FP64 instructions of the sum-factorized
 // bodies, and its upper triangle (36 and 378 values) is no larger than the

@@ -89,7 +89,7 @@ __device__ __forceinline__ bool apply_skipped(const ApplyParams<T> &prm) {
 // exactly, a*b = p + e (FMA), p is added to hi by TwoSum and the rounding
 // errors are collected in lo (Dekker 1971; Ogita, Rump & Oishi 2005) -- so
 // that the FP32 kernel neither loses p^T A p to cancellation between a node's
-// terms nor uses the 1/64-rate FP64 pipe per term.
+// terms nor uses the 1/73-rate FP64 pipe per term.
 template <typename T>
 struct DotAcc {
   T v = 0;
