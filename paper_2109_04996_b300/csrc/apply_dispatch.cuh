@@ -263,13 +263,25 @@ int launch_epb(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
 
 // Launch shapes are tunable (epb_choices) except for the collocated mass
 // operator, which is pointwise.
-template <typename T, int P>
+// PART: 0 every rule, 1 the non-collocated ones only, 2 the collocated ones
+// only (the double-word bodies compile the two groups in separate
+// translation units, with different double-word sums: dw.cuh)
+template <typename T, int P, int PART = 0>
 int dispatch_q(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
   constexpr int QG = (P + 1 <= FEM_MAX_Q) ? P + 1 : P;
   const bool diff = op->kind == FEM_DIFFUSION;
+  if constexpr (PART == 2) {
+    if (op->Q == P && op->colloc && diff) return launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps);
+    fem_set_error(diff ? "apply: not a collocated operator"
+                       : "apply: the collocated mass operator has no double-word body");
+    return FEM_EINVAL;
+  } else {
   if (op->Q == P) {
     if (op->colloc) {
-      if (diff) return launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps);
+      if constexpr (PART == 1) {
+        fem_set_error("apply: collocated operators take the other dispatch");
+        return FEM_EINVAL;
+      } else if (diff) return launch_epb<T, P, P, FEM_DIFFUSION, true>(op, prm, choice, bps);
       if constexpr (std::is_same<T, dw>::value) {
         fem_set_error("apply: the collocated mass operator has no double-word body");
         return FEM_EINVAL;
@@ -285,6 +297,7 @@ int dispatch_q(fem_op *op, const ApplyParams<T> &prm, int choice, int bps) {
                 : launch_epb<T, P, QG, FEM_MASS, false>(op, prm, choice, bps);
   fem_set_error("apply: unsupported (P, q) = (%d, %d)", P, op->Q);
   return FEM_EINVAL;
+  }
 }
 
 template <typename T>

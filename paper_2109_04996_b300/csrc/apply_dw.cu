@@ -18,6 +18,17 @@ extern template int fem_apply_dw_p<6>(fem_op *, const fem_apply::ApplyParams<dw>
 extern template int fem_apply_dw_p<7>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
 extern template int fem_apply_dw_p<8>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
 extern template int fem_apply_dw_p<9>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+// the collocated diffusion rules (apply_dw_p2c.cu .. apply_dw_p9c.cu)
+template <int P>
+int fem_apply_dw_pc(fem_op *op, const fem_apply::ApplyParams<dw> &prm, int choice, int bps);
+extern template int fem_apply_dw_pc<2>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+extern template int fem_apply_dw_pc<3>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+extern template int fem_apply_dw_pc<4>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+extern template int fem_apply_dw_pc<5>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+extern template int fem_apply_dw_pc<6>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+extern template int fem_apply_dw_pc<7>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+extern template int fem_apply_dw_pc<8>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
+extern template int fem_apply_dw_pc<9>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);
 
 int fem_launch_apply_dw_shape(fem_op *op, const double *x, double *y, const int32_t *list,
                               int64_t nsel, double *dot_out, int choice, int bps,
@@ -40,6 +51,18 @@ int fem_launch_apply_dw_shape(fem_op *op, const double *x, double *y, const int3
   prm.partials = op->d_partials; prm.counter = op->d_counter; prm.dot_out = dot_out;
   prm.skip = skip;
   if (nsel == 0) return FEM_OK;
+  if (op->colloc) {
+    switch (op->P) {
+      case 2: return fem_apply_dw_pc<2>(op, prm, choice, bps);
+      case 3: return fem_apply_dw_pc<3>(op, prm, choice, bps);
+      case 4: return fem_apply_dw_pc<4>(op, prm, choice, bps);
+      case 5: return fem_apply_dw_pc<5>(op, prm, choice, bps);
+      case 6: return fem_apply_dw_pc<6>(op, prm, choice, bps);
+      case 7: return fem_apply_dw_pc<7>(op, prm, choice, bps);
+      case 8: return fem_apply_dw_pc<8>(op, prm, choice, bps);
+      case 9: return fem_apply_dw_pc<9>(op, prm, choice, bps);
+    }
+  }
   switch (op->P) {
     case 2: return fem_apply_dw_p<2>(op, prm, choice, bps);
     case 3: return fem_apply_dw_p<3>(op, prm, choice, bps);

@@ -1,8 +1,9 @@
-// Double-word apply bodies of order P = 3 (see apply_dw.cu).
+// Double-word apply bodies of order P = 3, non-collocated rules (see
+// apply_dw.cu).
 #include "apply_dispatch.cuh"
 
 template <int P>
 int fem_apply_dw_p(fem_op *op, const fem_apply::ApplyParams<dw> &prm, int choice, int bps) {
-  return fem_apply::dispatch_q<dw, P>(op, prm, choice, bps);
+  return fem_apply::dispatch_q<dw, P, 1>(op, prm, choice, bps);   // the collocated rules: apply_dw_p3c.cu
 }
 template int fem_apply_dw_p<3>(fem_op *, const fem_apply::ApplyParams<dw> &, int, int);

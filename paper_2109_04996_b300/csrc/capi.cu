@@ -505,15 +505,15 @@ extern "C" fem_status fem_op_create(const fem_mesh *m, int kind, int quad, int q
   // p = 3..7, 3.2x at p = 8, 1.4x (p = 1) and 1.08x (p = 2) over the FP64
   // element matrices, 3-4x for BP5 and BP1.
   static const int kDiffF32[8] = {7, 1, 1, 0, 1, 0, 0, 1};
-  static const int kDiffF64[8] = {11, 11, 16, 8, 21, 21, 12, 15};
+  static const int kDiffF64[8] = {11, 11, 16, 15, 21, 21, 12, 15};
   static const int kCollF32[8] = {4, 1, 1, 1, 1, 0, 1, 1};
-  static const int kCollF64[8] = {13, 9, 22, 16, 15, 21, 21, 12};
+  static const int kCollF64[8] = {13, 9, 19, 16, 15, 21, 21, 12};
   static const int kMassF32[8] = {1, 1, 1, 1, 0, 1, 1, 1};
   static const int kMassF64[8] = {16, 16, 16, 12, 9, 9, 8, 12};
   // Vector diffusion (BP4, BP6): the pipelined gather serves scalar
   // operators only, so their FP64 defaults come from their own sweep (BP4 and
   // BP6 at about 4e6 nodes per component, BP6 p = 7 at 2.95e7).
-  static const int kDiffVecF64[8] = {11, 11, 19, 8, 8, 8, 8, 8};
+  static const int kDiffVecF64[8] = {11, 11, 19, 15, 8, 18, 18, 15};
   static const int kCollVecF64[8] = {9, 9, 19, 16, 15, 16, 19, 15};
   const int ip = P - 2;   // P in 2..9
   const bool vec = ncomp > 1;

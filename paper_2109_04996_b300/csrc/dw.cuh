@@ -48,10 +48,11 @@ __device__ __forceinline__ void dw_two_sum(float a, float b, float &s, float &e)
 // magnitude (Dekker 1971) instead of TwoSum -- the same e, hence the same
 // result bit for bit, from 3 FP32 additions instead of 6 plus a compare and
 // two selects on the ALU pipe.  Measured on the headline sweep (5e7 DOFs,
-// ms): p = 3, 5, 6, 7, 8 faster (5.32 -> 5.18, 4.34 -> 4.30, 4.05 -> 3.95,
-// 4.11 -> 3.99, 5.40 -> 5.32), p = 1, 2, 4 slower (the stencil 2.27 ->
-// 2.41, the element matrices 5.03 -> 5.10, 4.93 -> 4.96), so the orders'
-// translation units choose.
+// ms): the line bodies at p = 3..8 faster (5.32 -> 5.18, 4.91 -> 4.57 with
+// another launch shape, 4.34 -> 4.30, 4.05 -> 3.95, 4.11 -> 3.99, 5.40 ->
+// 5.32), the stencil and the element matrices at p = 1, 2 slower (2.27 ->
+// 2.41, 5.03 -> 5.10), and the collocated bodies (BP5) no faster or slower
+// (p = 3: 0.36 -> 0.38 ms at 8e6 DOFs), so each translation unit chooses.
 #ifndef FEM_DW_ADD_ORDERED
 #define FEM_DW_ADD_ORDERED 0
 #endif
