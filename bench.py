@@ -181,14 +181,14 @@ def measured_peaks():
 # matrices, indices and the two vectors, all proportional to the mesh), so
 # the full-size traffic is that ratio times the full-size algorithmic bytes.
 APPLY_F64_DRAM = {
-    1: (3944312, 4019679, 945628672, 4672512),
-    2: (493039, 4019679, 1690668288, 74403584),
-    3: (148877, 4096000, 1001657600, 34000384),
-    4: (59319, 3869893, 712023808, 30799104),
-    5: (32768, 4173281, 668073728, 32089600),
-    6: (17576, 3869893, 619112192, 29319168),
-    7: (12167, 4251528, 518859008, 30481408),
-    8: (8000, 4173281, 494781440, 158579456),
+    1: (3944312, 4019679, 948003328, 5165312),
+    2: (493039, 4019679, 1690484736, 74309632),
+    3: (148877, 4096000, 1001539584, 34050816),
+    4: (59319, 3869893, 711564288, 31769088),
+    5: (32768, 4173281, 670284544, 32340992),
+    6: (17576, 3869893, 617505792, 29090560),
+    7: (12167, 4251528, 518869248, 29997824),
+    8: (8000, 4173281, 494480128, 157703680),
 }
 
 
